@@ -1,0 +1,45 @@
+"""Pins of the exact gradient d log P(m) / d p_j (P(m) = sum_L p_{m,L})."""
+import numpy as np
+
+from td_inputs import repetition_phenomenological, rotated_phenomenological, sample_shots
+from oracle import exact
+
+
+def _posterior_marginals(dem, m):
+    """P(x_j = 1 | m) by enumerating every error pattern (tiny problems)."""
+    n = dem.n_mech
+    X = ((np.arange(1 << n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
+    H = dem.H_dense()
+    ok = np.all((X @ H.T) % 2 == m[None, :], axis=1)
+    p = dem.p
+    w = np.prod(np.where(X == 1, p, 1 - p), axis=1) * ok
+    return (w[:, None] * X).sum(axis=0) / w.sum()
+
+
+def test_gradient_matches_posterior_marginals():
+    """d log P / d p_j = pi_j / p_j - (1 - pi_j) / (1 - p_j), pi_j the posterior marginal."""
+    dem = repetition_phenomenological(4, 2, 0.08, 0.05)
+    rng = np.random.default_rng(3)
+    dem = dem.with_rates(rng.uniform(0.01, 0.2, dem.n_mech))
+    det, _ = sample_shots(dem, 5, seed=13)
+    g = exact.grad_total_logprob(dem, det)
+    for b in range(len(det)):
+        pi = _posterior_marginals(dem, det[b])
+        expect = pi / dem.p - (1 - pi) / (1 - dem.p)
+        np.testing.assert_allclose(g[b], expect, rtol=1e-9, atol=1e-9)
+
+
+def test_gradient_matches_central_differences():
+    dem = rotated_phenomenological(3, 1, 0.05, 0.03)
+    rng = np.random.default_rng(4)
+    dem = dem.with_rates(np.exp(rng.uniform(np.log(1e-3), np.log(1e-2), dem.n_mech)) * 5)
+    det, _ = sample_shots(dem, 3, seed=14)
+    g = exact.grad_total_logprob(dem, det)
+    lay = exact.Layering(dem)
+    for j in (0, 5, 17, dem.n_mech - 1):
+        h = 1e-6 * dem.p[j]
+        pp = dem.p.copy(); pp[j] += h
+        pm = dem.p.copy(); pm[j] -= h
+        fp = exact.total_logprob(exact.transfer_matrix(dem.with_rates(pp), det, lay))
+        fm = exact.total_logprob(exact.transfer_matrix(dem.with_rates(pm), det, lay))
+        np.testing.assert_allclose(g[:, j], (fp - fm) / (2 * h), rtol=1e-6, atol=1e-6)
