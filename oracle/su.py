@@ -32,6 +32,7 @@ Readings taken where the paper is silent (each also listed in the design doc):
   * Truncation: keep s_i > cutoff * s_1, at most chi; if the cut falls inside a
     multiplet (s_k - s_{k+1} <= mrtol * s_1), drop the whole multiplet.  lambda = s / s_1
     and ln s_1 goes to the log-scale.
+  * A class whose truncated weight comes out <= 0 gets log p = -inf.
   * Final contraction: every site's physical leg is read out into (class bit c_s), sqrt
     of each lambda is absorbed on both sides, rows are absorbed into a boundary MPS by
     zip-up (SVD truncation to chi_mps column by column), the class parity flows along
@@ -408,8 +409,10 @@ def _one_shot(plan, m, chi, chi_mps, cutoff, mrtol):
         if l:
             Z = np.array([(1 - p) * Z[0] + p * Z[1], (1 - p) * Z[1] + p * Z[0]])
     off = int(np.bitwise_xor.reduce(m.astype(np.int64))) if plan.offset_all else 0
+    # a class whose contracted weight is not positive (possible only through truncation
+    # error, the exact weight is a sum of probabilities) is reported as log 0 = -inf
     with np.errstate(divide="ignore"):
-        logZ = np.log(Z) + ls + peps.logscale
+        logZ = np.log(np.where(Z > 0, Z, 0.0)) + ls + peps.logscale
     return np.array([logZ[0 ^ off], logZ[1 ^ off]])
 
 
