@@ -1,0 +1,168 @@
+/*
+ * td.h -- tensor-network coset decoding of 3D codes on one GB300 (sm_103a).
+ *
+ * C ABI of libtd.so.  The problem statement is the detector error model (DEM) of Sec. 2.4
+ * of "Tensor Network Decoding Beyond 2D" (Piveteau, Chubb, Renes; arXiv 2310.10722):
+ * n mechanisms, each occurring independently with probability p_j and flipping the
+ * detectors of column j of H and the logical observables of column j of l.  For an
+ * observed detector outcome m the library returns, for every class L,
+ *
+ *     log p_{m,L},   p_{m,L} = sum_{x : Hx = m, l.x = L} prod_j p_j^{x_j} (1-p_j)^{1-x_j}
+ *
+ * (Sec. 2.4), evaluated approximately by the contraction of Sec. 4: the detector network
+ * (Sec. 3.1, 3.4) is swept layer by layer with a PEPS boundary whose bonds are truncated
+ * to chi by simple update after every gate, and the final 2D network is contracted by an
+ * MPS of bond chi_mps.  With chi and chi_mps at least the untruncated bond dimensions the
+ * result is exact.  The decision is argmax_L p_{m,L} (Sec. 2.4, L*(m)).
+ *
+ * Conventions common to every call
+ *   - Host pointers: DEM and layout arrays (read during td_build_network only; the
+ *     library keeps its own copy).  Device pointers: per-shot inputs and outputs of the
+ *     decoding calls; they must be CUDA device memory of the current device.
+ *   - Ownership: the caller owns every buffer it passes.  The library owns the opaque
+ *     td_network and its device workspace (allocated by td_build_network, freed by
+ *     td_free_network).
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Decoding calls
+ *     enqueue their work on it and return without synchronising, except the *_host
+ *     variants, which synchronise on it before returning.  A network is not thread safe:
+ *     use one network per concurrent stream.
+ *   - Errors: every call returns a td_status; td_last_error() describes the last failure
+ *     of the calling thread.  Argument errors are detected on the host before any work is
+ *     enqueued.  No call aborts the process or throws across the ABI.
+ */
+#ifndef TD_H_
+#define TD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TD_OK = 0,
+  TD_ERR_INVALID = 1,      /* bad argument: shapes, bits not in {0,1}, p outside [0,1] */
+  TD_ERR_NONLOCAL = 2,     /* a mechanism is not single-site, grid-bond or vertical */
+  TD_ERR_OOM = 3,          /* device or host allocation failed */
+  TD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  TD_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+  TD_ERR_NUMERIC = 6,      /* reserved: non-finite intermediate */
+  TD_ERR_UNSUPPORTED = 7   /* valid input outside what this build implements */
+} td_status;
+
+typedef enum {
+  TD_FP64 = 0,   /* FP64 storage and arithmetic everywhere (the plain FP64 GPU path) */
+  TD_FP32 = 1,   /* FP32 storage and contractions; FP64 truncation cores and log-sum */
+  TD_TF32 = 2    /* FP32 storage, layer contractions on tcgen05 (TF32 in, FP32 accumulate);
+                    FP64 truncation cores and log-sum */
+} td_precision;
+
+/* DEM triple (H, p, l) of Sec. 2.4, host memory, CSR by rows. */
+typedef struct {
+  int32_t n_det;             /* detectors (rows of H) */
+  int32_t n_mech;            /* error mechanisms (columns of H) */
+  int32_t n_obs;             /* logical observables (rows of l); this build supports 1 */
+  const int32_t* H_indptr;   /* [n_det + 1] */
+  const int32_t* H_indices;  /* [H_indptr[n_det]] mechanism indices of each detector */
+  const int32_t* L_indptr;   /* [n_obs + 1] */
+  const int32_t* L_indices;  /* [L_indptr[n_obs]] mechanism indices of each observable */
+  const double* p;           /* [n_mech], each in [0, 1] */
+} td_dem;
+
+/* Space-time layout: integer coordinates (x, y, t) of every detector, host memory,
+ * [n_det][3] row-major.  t is the layer (sweep direction, Sec. 4), (x, y) the site of a
+ * 2D grid.  Every occupied (x, y) must hold exactly one detector in every layer. */
+typedef struct {
+  const int32_t* det_xyt;
+} td_layout;
+
+typedef struct {
+  int32_t chi;             /* simple-update bond cap (Sec. 4; chi_SU of Sec. 5) */
+  int32_t chi_mps;         /* final boundary-MPS bond cap (chi_MPS of Sec. 5) */
+  int32_t precision;       /* td_precision */
+  int32_t ckpt_stride;     /* reserved for the adjoint sweep (layers between checkpoints) */
+  double svd_cutoff;       /* keep singular values s_i > svd_cutoff * s_1 */
+  double multiplet_rtol;   /* a cut inside s_k - s_{k+1} <= rtol * s_1 drops the multiplet */
+  double gram_cutoff;      /* drop Gram eigen-directions below gram_cutoff * max eigenvalue;
+                              negative: 1e-15 for TD_FP64, 1e-7 otherwise */
+  size_t mem_budget;       /* device workspace cap in bytes (0: 16 GiB) */
+  int32_t max_wave;        /* shots processed per wave (0: as many as mem_budget allows) */
+} td_options;
+
+typedef struct td_network td_network;
+
+typedef struct {
+  int32_t n_sites, n_layers, n_bonds, n_gates, n_counter_sites;
+  int32_t nx, ny;
+  int32_t wave;              /* shots per wave */
+  int32_t chi, chi_mps, precision;
+  int32_t offset_all;        /* 1 if the observable was replaced by l + sum of rows of H */
+  size_t workspace_bytes;    /* device bytes held by the network */
+  int64_t launches_per_wave; /* kernel launches enqueued per wave */
+} td_network_info;
+
+/* Fill `opt` with defaults: chi 8, chi_mps 16, TD_FP64, svd_cutoff 1e-12,
+ * multiplet_rtol 1e-8, gram_cutoff -1 (per precision), mem_budget 16 GiB. */
+void td_default_options(td_options* opt);
+
+/* Build the layered network of the DEM (Sec. 3.4 detector network in the layered form of
+ * Sec. 4; Sec. 2.4 merging of mechanisms with identical detectors and class effect) and
+ * allocate its device workspace.  Errors: TD_ERR_INVALID (shapes, ranges),
+ * TD_ERR_NONLOCAL (a two-detector mechanism whose detectors are neither grid neighbours
+ * in one layer nor one site in consecutive layers, or a mechanism with > 2 detectors),
+ * TD_ERR_UNSUPPORTED (n_obs != 1, chi > 32, missing detector at some (site, layer)),
+ * TD_ERR_OOM, TD_ERR_CUDA.  On success *out owns the network. */
+td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_options* opt,
+                           td_network** out);
+
+/* Coset log-probabilities (Sec. 2.4 p_{m,L}; Sec. 4 contraction).
+ * det_dev: device uint8 [B][n_det], each 0 or 1 (detector outcomes m).
+ * logp_dev: device double [B][2^n_obs]; logp_dev[b][L] = log p_{m_b, L} (-inf if zero).
+ * B >= 0 (B = 0 is a no-op).  Asynchronous on `stream`. */
+td_status td_coset_logprob(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
+                           void* stream);
+
+/* Decisions L*(m) = argmax_L p_{m,L} (Sec. 2.4; ties -> lowest L) and margins
+ * log p_{m,L*} - max_{L != L*} log p_{m,L}.  decision_dev: device int32 [B];
+ * margin_dev: device double [B] or NULL.  Asynchronous on `stream`. */
+td_status td_decode(td_network* net, const uint8_t* det_dev, int64_t B, int32_t* decision_dev,
+                    double* margin_dev, void* stream);
+
+/* td_coset_logprob with host buffers: det_host uint8 [B][n_det] and logp_host double
+ * [B][2^n_obs] in host memory (pinned memory gives asynchronous copies).  Copies in, runs
+ * and copies out on `stream` in waves; synchronises before returning. */
+td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_t B,
+                                double* logp_host, void* stream);
+
+/* Gradient of the mean total log-probability (1/B) sum_b log P(m_b), P(m) = sum_L p_{m,L},
+ * with respect to every mechanism rate (the adjoint of the Sec. 4 sweep).  p_dev: device
+ * double [n_mech] rates to use (NULL: the build rates); logP_dev: device double [B];
+ * grad_dev: device double [n_mech].  Not implemented in this build: returns
+ * TD_ERR_UNSUPPORTED. */
+td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev,
+                          double* logP_dev, double* grad_dev, void* stream);
+
+td_status td_network_get_info(const td_network* net, td_network_info* info);
+
+/* Diagnostic: run the sweep of Sec. 4 on the first min(B, wave) shots up to the end of the
+ * gate round that contains gate n_gates-1 (site-local operators of a layer run before its
+ * first round), then copy the bond weights and the log-scale accumulators.
+ * lam_dev: device double [B][n_bonds][chi] (lambda of each bond, zero padded; bonds in
+ * the order of their (site a, site b) pairs, sites ordered by (y, x));
+ * logacc_dev: device double [B][n_sites + n_bonds + 1] or NULL.  Returns the number of
+ * gates applied in *applied.  Asynchronous on `stream`. */
+td_status td_debug_sweep(td_network* net, const uint8_t* det_dev, int64_t B, int32_t n_gates, double* lam_dev,
+                         double* logacc_dev, int32_t* applied, void* stream);
+
+/* Release the network and its device workspace (NULL is a no-op).  The caller must
+ * ensure no enqueued work still uses it. */
+void td_free_network(td_network* net);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* td_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TD_H_ */

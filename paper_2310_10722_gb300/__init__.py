@@ -1,0 +1,161 @@
+"""GB300-native tensor-network coset decoder (arXiv 2310.10722), Python binding.
+
+Thin argument marshalling over the C ABI of libtd.so (include/td.h): every step of the
+decoding path runs in the library's CUDA kernels.  PyTorch supplies device memory and
+streams.  Importing this package does not load the library; the first Network does, and
+raises if libtd.so has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import TD_FP32, TD_FP64, TD_TF32, TDError, check
+
+__all__ = ["Network", "TDError", "TD_FP64", "TD_FP32", "TD_TF32", "load_library"]
+
+
+def load_library():
+    return _lib.load()
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+class Network:
+    """A built decoding network (td_build_network) and its device workspace.
+
+    H and l are given in CSR by rows (detectors x mechanisms, observables x mechanisms),
+    `p` the mechanism rates, `det_xyt` the (x, y, t) of every detector.
+    """
+
+    def __init__(self, H_indptr, H_indices, L_indptr, L_indices, p, det_xyt, *, n_mech=None,
+                 chi=8, chi_mps=16, precision=TD_FP64, svd_cutoff=1e-12, multiplet_rtol=1e-8,
+                 gram_cutoff=None, mem_budget=0, max_wave=0):
+        lib = _lib.load()
+        self._lib = lib
+        self._keep = [_i32(H_indptr), _i32(H_indices), _i32(L_indptr), _i32(L_indices),
+                      np.ascontiguousarray(np.asarray(p, dtype=np.float64)), _i32(det_xyt).reshape(-1)]
+        hip, hix, lip, lix, pp, xyt = self._keep
+        n_det = len(hip) - 1
+        n_obs = len(lip) - 1
+        n_mech = len(pp) if n_mech is None else n_mech
+        P = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+        dem = _lib.td_dem(n_det, n_mech, n_obs, P(hip, C.c_int32), P(hix, C.c_int32), P(lip, C.c_int32),
+                          P(lix, C.c_int32), P(pp, C.c_double))
+        lay = _lib.td_layout(P(xyt, C.c_int32))
+        opt = _lib.td_options()
+        lib.td_default_options(C.byref(opt))
+        opt.chi, opt.chi_mps, opt.precision = chi, chi_mps, precision
+        opt.svd_cutoff, opt.multiplet_rtol = svd_cutoff, multiplet_rtol
+        if gram_cutoff is not None:
+            opt.gram_cutoff = gram_cutoff
+        if mem_budget:
+            opt.mem_budget = mem_budget
+        opt.max_wave = max_wave
+        h = C.c_void_p()
+        check(lib.td_build_network(C.byref(dem), C.byref(lay), C.byref(opt), C.byref(h)))
+        self._h = h
+        self.n_det, self.n_mech, self.n_obs = n_det, n_mech, n_obs
+        self.n_class = 1 << n_obs
+
+    @classmethod
+    def from_dem(cls, dem, **kw):
+        """Build from any object with H_csr(), L_csr(), p, det_xyt (e.g. td_inputs.DEM)."""
+        hip, hix = dem.H_csr()
+        lip, lix = dem.L_csr()
+        return cls(hip, hix, lip, lix, dem.p, dem.det_xyt, n_mech=dem.n_mech, **kw)
+
+    def info(self) -> dict:
+        inf = _lib.td_network_info()
+        check(self._lib.td_network_get_info(self._h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def _check_det(self, det):
+        import torch
+        if not (isinstance(det, torch.Tensor) and det.is_cuda and det.dtype == torch.uint8 and det.dim() == 2
+                and det.shape[1] == self.n_det and det.is_contiguous()):
+            raise ValueError(f"det must be a contiguous CUDA uint8 tensor [B, {self.n_det}]")
+
+    def coset_logprob(self, det, out=None, stream=None):
+        """log p_{m,L} for every shot: CUDA float64 [B, 2^n_obs]."""
+        import torch
+        self._check_det(det)
+        B = det.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n_class), dtype=torch.float64, device=det.device)
+        check(self._lib.td_coset_logprob(self._h, C.c_void_p(det.data_ptr()), B, C.c_void_p(out.data_ptr()),
+                                         self._stream(stream)))
+        return out
+
+    def decode(self, det, stream=None):
+        """(decision int32 [B], margin float64 [B]) on the device."""
+        import torch
+        self._check_det(det)
+        B = det.shape[0]
+        dec = torch.empty(B, dtype=torch.int32, device=det.device)
+        mar = torch.empty(B, dtype=torch.float64, device=det.device)
+        check(self._lib.td_decode(self._h, C.c_void_p(det.data_ptr()), B, C.c_void_p(dec.data_ptr()),
+                                  C.c_void_p(mar.data_ptr()), self._stream(stream)))
+        return dec, mar
+
+    def coset_logprob_host(self, det, out=None, stream=None):
+        """Host-buffer variant: det uint8 [B, n_det] (numpy or CPU tensor, ideally pinned);
+        returns float64 [B, 2^n_obs] in host memory.  Synchronises the stream."""
+        import torch
+        if isinstance(det, np.ndarray):
+            det = torch.from_numpy(np.ascontiguousarray(det, dtype=np.uint8))
+        if det.is_cuda or det.dtype != torch.uint8 or det.dim() != 2 or det.shape[1] != self.n_det:
+            raise ValueError(f"det must be a host uint8 tensor [B, {self.n_det}]")
+        det = det.contiguous()
+        B = det.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n_class), dtype=torch.float64, pin_memory=det.is_pinned())
+        check(self._lib.td_coset_logprob_host(self._h, C.c_void_p(det.data_ptr()), B,
+                                              C.c_void_p(out.data_ptr()), self._stream(stream)))
+        return out
+
+    def grad_logprob(self, det, p=None, stream=None):
+        import torch
+        self._check_det(det)
+        B = det.shape[0]
+        logP = torch.empty(B, dtype=torch.float64, device=det.device)
+        grad = torch.empty(self.n_mech, dtype=torch.float64, device=det.device)
+        pp = C.c_void_p(p.data_ptr()) if p is not None else None
+        check(self._lib.td_grad_logprob(self._h, C.c_void_p(det.data_ptr()), B, pp, C.c_void_p(logP.data_ptr()),
+                                        C.c_void_p(grad.data_ptr()), self._stream(stream)))
+        return logP, grad
+
+    def debug_sweep(self, det, n_gates, stream=None):
+        """Bond weights [B, n_bonds, chi] and log-scale slots after the first n_gates gates
+        (rounded up to a whole gate round); returns (lam, logacc, applied)."""
+        import torch
+        self._check_det(det)
+        inf = self.info()
+        B = min(det.shape[0], inf["wave"])
+        lam = torch.zeros((B, inf["n_bonds"], inf["chi"]), dtype=torch.float64, device=det.device)
+        la = torch.zeros((B, inf["n_sites"] + inf["n_bonds"] + 1), dtype=torch.float64, device=det.device)
+        applied = C.c_int32()
+        check(self._lib.td_debug_sweep(self._h, C.c_void_p(det.data_ptr()), B, n_gates, C.c_void_p(lam.data_ptr()),
+                                       C.c_void_p(la.data_ptr()), C.byref(applied), self._stream(stream)))
+        return lam, la, applied.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.td_free_network(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

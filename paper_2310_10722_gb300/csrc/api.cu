@@ -1,0 +1,369 @@
+// C ABI of libtd (include/td.h): network construction, device workspace, and the launch
+// sequence of one decoding call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sweep.cuh"
+#include "td_internal.h"
+
+namespace {
+thread_local std::string g_err;
+
+td_status fail(td_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+td_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(TD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+}  // namespace
+
+struct td_network {
+  td::Plan plan;
+  int32_t wave = 0;
+  size_t elem = 8;            // bytes per storage element
+  void* d_gamma = nullptr;
+  double* d_lam = nullptr;
+  double* d_logacc = nullptr;
+  void* d_gram = nullptr;
+  double* d_tbuf = nullptr;
+  double* d_t1buf = nullptr;   // refinement transforms (FP32 storage only)
+  void* d_fscr = nullptr;
+  double* d_Z = nullptr;
+  td::GateDesc* d_gates = nullptr;
+  td::LocalDesc* d_locals = nullptr;
+  td::FinalSite* d_finals = nullptr;
+  int32_t* d_grid = nullptr;
+  uint8_t* d_det_stage = nullptr;
+  double* d_logp_stage = nullptr;
+  int32_t nslots = 0;
+  td::FinalArgs fin{};
+  size_t bytes = 0;
+  int64_t launches_per_wave = 0;
+  std::vector<void*> allocs;
+
+  ~td_network() {
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename P>
+  bool alloc(P*& ptr, size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    allocs.push_back(p);
+    bytes += n;
+    ptr = reinterpret_cast<P*>(p);
+    return true;
+  }
+};
+
+extern "C" {
+
+void td_default_options(td_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->chi = 8;
+  opt->chi_mps = 16;
+  opt->precision = TD_FP64;
+  opt->ckpt_stride = 4;
+  opt->svd_cutoff = 1e-12;
+  opt->multiplet_rtol = 1e-8;
+  opt->gram_cutoff = -1.0;   // per precision
+  opt->mem_budget = size_t(16) << 30;
+  opt->max_wave = 0;
+}
+
+const char* td_last_error(void) { return g_err.c_str(); }
+
+td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_options* opt, td_network** out) {
+  g_err.clear();
+  if (!dem || !layout || !out) return fail(TD_ERR_INVALID, "null argument");
+  *out = nullptr;
+  td_options o;
+  if (opt) o = *opt; else td_default_options(&o);
+  td_network* net = new (std::nothrow) td_network();
+  if (!net) return fail(TD_ERR_OOM, "host allocation failed");
+  std::string err;
+  td_status st = td::build_plan(*dem, *layout, o, net->plan, err);
+  if (st != TD_OK) { delete net; return fail(st, err); }
+  td::Plan& P = net->plan;
+  if (P.nx > 32) { delete net; return fail(TD_ERR_UNSUPPORTED, "grid wider than 32 sites"); }
+  const int chi = P.chi, cm = P.chi_mps, Dm = P.max_final_D;
+  if ((int64_t)cm * Dm > 256) { delete net; return fail(TD_ERR_UNSUPPORTED, "chi_mps * final bond dimension must be <= 256"); }
+  if (o.precision == TD_TF32) { delete net; return fail(TD_ERR_UNSUPPORTED, "TF32 tensor-core path not built yet"); }
+  net->elem = (o.precision == TD_FP64) ? 8 : 4;
+  net->nslots = P.S + P.n_bonds + 1;
+
+  // final-contraction scratch per shot (elements of the accumulation type)
+  const int64_t cmx = std::max(cm, 2);
+  const int64_t mps_stride = ((int64_t)cm * Dm * cmx + 3) / 4 * 4;
+  const int64_t mC = (int64_t)cm * cmx * Dm * 2 + 4;
+  const int64_t mF = 2LL * Dm * Dm * Dm * Dm + 4;
+  const int64_t mT1 = (int64_t)cm * Dm * 2 * Dm * cmx + 4;
+  const int64_t mT = (int64_t)cm * Dm * cmx * Dm * 2 + (int64_t)cm * Dm + 8;   // + ordering scratch
+  const int64_t mG = (int64_t)cm * Dm * cmx * Dm * 2 + 4;      // M^T, n x m
+  int64_t acc = 0;
+  auto take = [&](int64_t n) { int64_t r = acc; acc += (n + 3) / 4 * 4; return r; };
+  net->fin.off_mps0 = take(mps_stride * P.nx);
+  net->fin.off_mps1 = take(mps_stride * P.nx);
+  net->fin.mps_stride = mps_stride;
+  net->fin.off_C0 = take(mC);
+  net->fin.off_C1 = take(mC);
+  net->fin.off_F = take(mF);
+  net->fin.off_T1 = take(mT1);
+  net->fin.off_T = take(mT);
+  net->fin.off_G = take(mG);
+  net->fin.off_V = take((int64_t)cm * Dm * cm * Dm + 4);
+  net->fin.off_s = take(2 * (int64_t)cm * Dm + 4);
+  net->fin.scratch_elems = acc;
+
+  const size_t per_shot = P.shot_elems * net->elem + (size_t)P.n_bonds * chi * 8 + (size_t)net->nslots * 8 +
+                          (size_t)P.max_round_gates * 4 * chi * chi * (net->elem + 8 + (o.precision == TD_FP64 ? 0 : 16)) +
+                          (size_t)acc * net->elem + 16 + (size_t)P.n_det + 16;
+  const size_t budget = o.mem_budget ? o.mem_budget : (size_t(16) << 30);
+  int64_t wave = (int64_t)(budget / std::max<size_t>(per_shot, 1));
+  if (o.max_wave > 0) wave = std::min<int64_t>(wave, o.max_wave);
+  wave = std::min<int64_t>(wave, 65535);
+  if (wave < 1) { delete net; return fail(TD_ERR_OOM, "mem_budget too small for one shot"); }
+  net->wave = (int32_t)wave;
+
+  bool ok = net->alloc(net->d_gamma, (size_t)wave * P.shot_elems * net->elem) &&
+            net->alloc(net->d_lam, (size_t)wave * P.n_bonds * chi * 8) &&
+            net->alloc(net->d_logacc, (size_t)wave * net->nslots * 8) &&
+            net->alloc(net->d_gram, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * net->elem) &&
+            net->alloc(net->d_tbuf, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * 8) &&
+            (o.precision == TD_FP64 ||
+             net->alloc(net->d_t1buf, (size_t)std::max(P.max_round_gates, 1) * wave * 8 * chi * chi * 8)) &&
+            net->alloc(net->d_fscr, (size_t)wave * acc * net->elem) &&
+            net->alloc(net->d_Z, (size_t)wave * 2 * 8) &&
+            net->alloc(net->d_gates, sizeof(td::GateDesc) * P.gates.size()) &&
+            net->alloc(net->d_locals, sizeof(td::LocalDesc) * P.locals.size()) &&
+            net->alloc(net->d_finals, sizeof(td::FinalSite) * P.finals.size()) &&
+            net->alloc(net->d_grid, sizeof(int32_t) * P.grid_site.size()) &&
+            net->alloc(net->d_det_stage, (size_t)wave * P.n_det) &&
+            net->alloc(net->d_logp_stage, (size_t)wave * 2 * 8);
+  if (!ok) { delete net; return fail(TD_ERR_OOM, "device allocation failed"); }
+  cudaError_t e;
+  if ((!P.gates.empty() && (e = cudaMemcpy(net->d_gates, P.gates.data(), sizeof(td::GateDesc) * P.gates.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (e = cudaMemcpy(net->d_locals, P.locals.data(), sizeof(td::LocalDesc) * P.locals.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(net->d_finals, P.finals.data(), sizeof(td::FinalSite) * P.finals.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(net->d_grid, P.grid_site.data(), sizeof(int32_t) * P.grid_site.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    delete net;
+    return cuda_fail(e, "descriptor upload");
+  }
+  // kernels need > 48 KiB of dynamic shared memory for chi > 16
+  const size_t smem_c = td::core_smem_bytes(chi);
+  (void)smem_c;
+  int64_t launches = 1 + 2;   // init, final, finalize
+  const int per_round = (o.precision == TD_FP64) ? 3 : 5;
+  for (const td::LayerPlan& L : P.layers) launches += 1 + per_round * (int64_t)L.rounds.size();
+  net->launches_per_wave = launches;
+  *out = net;
+  return TD_OK;
+}
+
+static td_status run(td_network* net, const uint8_t* det, int64_t B, double* logp, int32_t* decision, double* margin,
+                     cudaStream_t st) {
+  td::Plan& P = net->plan;
+  for (int64_t w0 = 0; w0 < B; w0 += net->wave) {
+    const int32_t Bw = (int32_t)std::min<int64_t>(net->wave, B - w0);
+    td::SweepArgs a{};
+    a.gamma = net->d_gamma;
+    a.shot_elems = P.shot_elems;
+    a.lam = net->d_lam;
+    a.logacc = net->d_logacc;
+    a.det = det;
+    a.nbonds = P.n_bonds;
+    a.chi = P.chi;
+    a.nslots = net->nslots;
+    a.n_det = P.n_det;
+    a.wave_first = (int32_t)w0;
+    a.B = Bw;
+    a.gram_cutoff = P.gram_cutoff;
+    a.svd_cutoff = P.svd_cutoff;
+    a.multiplet_rtol = P.multiplet_rtol;
+    const bool f64 = P.precision == TD_FP64;
+    cudaError_t e = f64 ? td::launch_sweep_init<double, double>(a, net->d_locals, P.S, st)
+                        : td::launch_sweep_init<float, float>(a, net->d_locals, P.S, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init launch");
+    for (int32_t t = 0; t < P.T; ++t) {
+      const td::LayerPlan& L = P.layers[t];
+      e = f64 ? td::launch_local<double, double>(a, net->d_locals + L.local_first, P.S, st)
+              : td::launch_local<float, float>(a, net->d_locals + L.local_first, P.S, st);
+      if (e != cudaSuccess) return cuda_fail(e, "local launch");
+      for (const td::Round& rd : L.rounds) {
+        e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, nullptr, P.S, st)
+                : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, net->d_t1buf, P.S, st);
+        if (e != cudaSuccess) return cuda_fail(e, "gate round launch");
+      }
+    }
+    td::FinalArgs f = net->fin;
+    f.gamma = net->d_gamma;
+    f.shot_elems = P.shot_elems;
+    f.lam = net->d_lam;
+    f.logacc = net->d_logacc;
+    f.sites = net->d_finals;
+    f.grid_site = net->d_grid;
+    f.scratch = net->d_fscr;
+    f.Z = net->d_Z;
+    f.nbonds = P.n_bonds;
+    f.chi = P.chi;
+    f.nslots = net->nslots;
+    f.slot = P.S + P.n_bonds;
+    f.nx = P.nx;
+    f.ny = P.ny;
+    f.chi_mps = P.chi_mps;
+    f.B = Bw;
+    f.svd_cutoff = P.svd_cutoff;
+    f.multiplet_rtol = P.multiplet_rtol;
+    e = f64 ? td::launch_final<double, double>(f, st) : td::launch_final<float, float>(f, st);
+    if (e != cudaSuccess) return cuda_fail(e, "final launch");
+    td::FinalizeArgs z{};
+    z.Z = net->d_Z;
+    z.logacc = net->d_logacc;
+    z.det = det;
+    z.logp = logp;
+    z.decision = decision;
+    z.margin = margin;
+    z.nslots = net->nslots;
+    z.n_det = P.n_det;
+    z.wave_first = (int32_t)w0;
+    z.B = Bw;
+    z.offset_all = P.offset_all;
+    for (int i = 0; i < 4; ++i) z.mix[i] = P.glob_mix[i];
+    e = td::launch_finalize(z, st);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
+  }
+  return TD_OK;
+}
+
+static td_status check_call(td_network* net, const void* det, int64_t B) {
+  if (!net) return fail(TD_ERR_INVALID, "null network");
+  if (B < 0) return fail(TD_ERR_INVALID, "B must be >= 0");
+  if (B > 0 && !det) return fail(TD_ERR_INVALID, "null detector buffer");
+  if (B > (int64_t)1 << 31) return fail(TD_ERR_INVALID, "B too large");
+  return TD_OK;
+}
+
+td_status td_coset_logprob(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev, void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (B > 0 && !logp_dev) return fail(TD_ERR_INVALID, "null output buffer");
+  return run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+td_status td_decode(td_network* net, const uint8_t* det_dev, int64_t B, int32_t* decision_dev, double* margin_dev,
+                    void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (B > 0 && !decision_dev) return fail(TD_ERR_INVALID, "null decision buffer");
+  return run(net, det_dev, B, nullptr, decision_dev, margin_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_t B, double* logp_host, void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_host, B);
+  if (s != TD_OK) return s;
+  if (B > 0 && !logp_host) return fail(TD_ERR_INVALID, "null output buffer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int32_t n_det = net->plan.n_det;
+  for (int64_t w0 = 0; w0 < B; w0 += net->wave) {
+    const int64_t Bw = std::min<int64_t>(net->wave, B - w0);
+    cudaError_t e = cudaMemcpyAsync(net->d_det_stage, det_host + w0 * n_det, (size_t)Bw * n_det,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "detector copy");
+    s = run(net, net->d_det_stage, Bw, net->d_logp_stage, nullptr, nullptr, st);
+    if (s != TD_OK) return s;
+    e = cudaMemcpyAsync(logp_host + w0 * 2, net->d_logp_stage, (size_t)Bw * 2 * sizeof(double),
+                        cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "result copy");
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return TD_OK;
+}
+
+td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev, double* logP_dev,
+                          double* grad_dev, void* stream) {
+  g_err.clear();
+  (void)det_dev; (void)B; (void)p_dev; (void)logP_dev; (void)grad_dev; (void)stream;
+  if (!net) return fail(TD_ERR_INVALID, "null network");
+  return fail(TD_ERR_UNSUPPORTED, "adjoint sweep not built yet");
+}
+
+td_status td_debug_sweep(td_network* net, const uint8_t* det_dev, int64_t B, int32_t n_gates, double* lam_dev,
+                         double* logacc_dev, int32_t* applied, void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (!lam_dev || !applied) return fail(TD_ERR_INVALID, "null output");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  td::Plan& P = net->plan;
+  const int32_t Bw = (int32_t)std::min<int64_t>(net->wave, B);
+  td::SweepArgs a{};
+  a.gamma = net->d_gamma; a.shot_elems = P.shot_elems; a.lam = net->d_lam; a.logacc = net->d_logacc;
+  a.det = det_dev; a.nbonds = P.n_bonds; a.chi = P.chi; a.nslots = net->nslots; a.n_det = P.n_det;
+  a.wave_first = 0; a.B = Bw;
+  a.gram_cutoff = P.gram_cutoff; a.svd_cutoff = P.svd_cutoff; a.multiplet_rtol = P.multiplet_rtol;
+  const bool f64 = P.precision == TD_FP64;
+  cudaError_t e = f64 ? td::launch_sweep_init<double, double>(a, net->d_locals, P.S, st)
+                      : td::launch_sweep_init<float, float>(a, net->d_locals, P.S, st);
+  if (e != cudaSuccess) return cuda_fail(e, "init launch");
+  int32_t done = 0;
+  for (int32_t t = 0; t < P.T && done < n_gates; ++t) {
+    const td::LayerPlan& L = P.layers[t];
+    e = f64 ? td::launch_local<double, double>(a, net->d_locals + L.local_first, P.S, st)
+            : td::launch_local<float, float>(a, net->d_locals + L.local_first, P.S, st);
+    if (e != cudaSuccess) return cuda_fail(e, "local launch");
+    for (const td::Round& rd : L.rounds) {
+      if (done >= n_gates) break;
+      e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, nullptr, P.S, st)
+              : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, net->d_t1buf, P.S, st);
+      if (e != cudaSuccess) return cuda_fail(e, "gate round launch");
+      done += rd.count;
+    }
+  }
+  e = cudaMemcpyAsync(lam_dev, net->d_lam, sizeof(double) * Bw * P.n_bonds * P.chi, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && logacc_dev)
+    e = cudaMemcpyAsync(logacc_dev, net->d_logacc, sizeof(double) * Bw * net->nslots, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "debug copy");
+  *applied = done;
+  return TD_OK;
+}
+
+td_status td_network_get_info(const td_network* net, td_network_info* info) {
+  if (!net || !info) return fail(TD_ERR_INVALID, "null argument");
+  const td::Plan& P = net->plan;
+  info->n_sites = P.S;
+  info->n_layers = P.T;
+  info->n_bonds = P.n_bonds;
+  info->n_gates = (int32_t)P.gates.size();
+  info->n_counter_sites = P.n_counter_sites;
+  info->nx = P.nx;
+  info->ny = P.ny;
+  info->wave = net->wave;
+  info->chi = P.chi;
+  info->chi_mps = P.chi_mps;
+  info->precision = P.precision;
+  info->offset_all = P.offset_all;
+  info->workspace_bytes = net->bytes;
+  info->launches_per_wave = net->launches_per_wave;
+  return TD_OK;
+}
+
+void td_free_network(td_network* net) { delete net; }
+
+}  // extern "C"

@@ -1,0 +1,402 @@
+// Host planner: DEM + layout -> layered detector network and its gate schedule.
+//
+// Follows Sec. 2.4 (DEM triple, merging of mechanisms with identical detectors and class
+// effect), Sec. 3.4 (a DEM's detector network: mechanisms are weighted equality nodes,
+// detectors parity nodes) and the layered form of Sec. 4 / Sec. 5.1 (natural split: a
+// mechanism between two checks of one layer is a two-site gate; mechanisms between layers
+// are contracted between layers).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+#include <tuple>
+
+#include "td_internal.h"
+
+namespace td {
+namespace {
+
+struct Mech {
+  std::vector<int32_t> dets;
+  int32_t l = 0;
+  double p = 0;
+  // classification
+  int kind = 0;      // 0 global, 1 single, 2 pair, 3 vertical
+  int32_t a = -1, b = -1, t = -1;
+};
+
+enum { kGlobal = 0, kSingle = 1, kPair = 2, kVert = 3 };
+
+// W[tau][dc]: probability that the XOR of a group's mechanism bits is tau and their class
+// flips XOR to dc.
+void parity_weights(const std::vector<const Mech*>& group, double W[2][2]) {
+  W[0][0] = 1; W[0][1] = 0; W[1][0] = 0; W[1][1] = 0;
+  for (const Mech* m : group) {
+    double N[2][2] = {{0, 0}, {0, 0}};
+    for (int tau = 0; tau < 2; ++tau)
+      for (int dc = 0; dc < 2; ++dc) {
+        N[tau][dc] += (1 - m->p) * W[tau][dc];
+        N[tau ^ 1][dc ^ m->l] += m->p * W[tau][dc];
+      }
+    std::memcpy(W, N, sizeof(N));
+  }
+}
+
+void matmul(int P, const double* A, const double* B, double* C) {  // C = A B
+  double tmp[kMaxPhys * kMaxPhys];
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) {
+      double s = 0;
+      for (int k = 0; k < P; ++k) s += A[i * P + k] * B[k * P + j];
+      tmp[i * P + j] = s;
+    }
+  std::memcpy(C, tmp, sizeof(double) * P * P);
+}
+
+void eye(int P, double* A) {
+  for (int i = 0; i < P * P; ++i) A[i] = 0;
+  for (int i = 0; i < P; ++i) A[i * P + i] = 1;
+}
+
+}  // namespace
+
+td_status build_plan(const td_dem& dem, const td_layout& layout, const td_options& opt, Plan& plan,
+                     std::string& err) {
+  // ---- validation ------------------------------------------------------------------
+  if (dem.n_det < 1 || dem.n_mech < 0 || dem.n_obs < 0) { err = "n_det must be >= 1, n_mech and n_obs >= 0"; return TD_ERR_INVALID; }
+  if (dem.n_obs != 1) { err = "this build supports exactly one logical observable (n_obs = 1)"; return TD_ERR_UNSUPPORTED; }
+  if (!dem.H_indptr || !dem.L_indptr || !dem.p || !layout.det_xyt ||
+      (!dem.H_indices && dem.H_indptr[dem.n_det] > 0) || (!dem.L_indices && dem.L_indptr[dem.n_obs] > 0)) {
+    err = "null DEM or layout array"; return TD_ERR_INVALID;
+  }
+  if (opt.chi < 1 || opt.chi > kMaxChi) { err = "chi must be in [1, 32]"; return opt.chi < 1 ? TD_ERR_INVALID : TD_ERR_UNSUPPORTED; }
+  if (opt.chi_mps < 1) { err = "chi_mps must be >= 1"; return TD_ERR_INVALID; }
+  if (opt.precision < TD_FP64 || opt.precision > TD_TF32) { err = "unknown precision"; return TD_ERR_INVALID; }
+  if (!(opt.svd_cutoff >= 0 && opt.svd_cutoff < 1) || !(opt.multiplet_rtol >= 0 && opt.multiplet_rtol < 1) ||
+      !(opt.gram_cutoff < 1)) { err = "cutoffs must be in [0, 1)"; return TD_ERR_INVALID; }
+  const int32_t n_det = dem.n_det, n_mech = dem.n_mech;
+  std::vector<std::vector<int32_t>> mdets(n_mech);
+  std::vector<int32_t> mobs(n_mech, 0);
+  if (dem.H_indptr[0] != 0) { err = "H_indptr[0] must be 0"; return TD_ERR_INVALID; }
+  for (int32_t i = 0; i < n_det; ++i) {
+    if (dem.H_indptr[i + 1] < dem.H_indptr[i]) { err = "H_indptr not monotone"; return TD_ERR_INVALID; }
+    for (int32_t k = dem.H_indptr[i]; k < dem.H_indptr[i + 1]; ++k) {
+      int32_t j = dem.H_indices[k];
+      if (j < 0 || j >= n_mech) { err = "H index out of range"; return TD_ERR_INVALID; }
+      if (std::find(mdets[j].begin(), mdets[j].end(), i) != mdets[j].end()) { err = "duplicate entry in H"; return TD_ERR_INVALID; }
+      mdets[j].push_back(i);
+    }
+  }
+  if (dem.L_indptr[0] != 0 || dem.L_indptr[1] < 0) { err = "bad L_indptr"; return TD_ERR_INVALID; }
+  for (int32_t k = dem.L_indptr[0]; k < dem.L_indptr[1]; ++k) {
+    int32_t j = dem.L_indices[k];
+    if (j < 0 || j >= n_mech) { err = "L index out of range"; return TD_ERR_INVALID; }
+    if (mobs[j]) { err = "duplicate entry in l"; return TD_ERR_INVALID; }
+    mobs[j] = 1;
+  }
+  for (int32_t j = 0; j < n_mech; ++j)
+    if (!(dem.p[j] >= 0.0 && dem.p[j] <= 1.0)) { err = "mechanism probability outside [0, 1]"; return TD_ERR_INVALID; }
+  for (int32_t i = 0; i < 3 * n_det; ++i)
+    if (layout.det_xyt[i] < 0 || layout.det_xyt[i] > (1 << 14)) { err = "detector coordinate outside [0, 16384]"; return TD_ERR_INVALID; }
+
+  // ---- sites and layers ----------------------------------------------------------------
+  plan = Plan();
+  plan.n_det = n_det; plan.n_mech = n_mech; plan.n_obs = dem.n_obs;
+  plan.chi = opt.chi; plan.chi_mps = opt.chi_mps; plan.precision = opt.precision;
+  plan.svd_cutoff = opt.svd_cutoff; plan.multiplet_rtol = opt.multiplet_rtol;
+  // Gram eigen-directions below this fraction of the largest are rounding noise: FP64
+  // Grams resolve ~1e-16 of the largest eigenvalue, the refined FP32 Gram ~1e-7.
+  plan.gram_cutoff = opt.gram_cutoff >= 0 ? opt.gram_cutoff : (opt.precision == TD_FP64 ? 1e-15 : 1e-7);
+  std::set<std::pair<int32_t, int32_t>> yx;
+  int32_t T = 0;
+  for (int32_t i = 0; i < n_det; ++i) {
+    yx.insert({layout.det_xyt[3 * i + 1], layout.det_xyt[3 * i]});
+    T = std::max(T, layout.det_xyt[3 * i + 2] + 1);
+    plan.nx = std::max(plan.nx, layout.det_xyt[3 * i] + 1);
+    plan.ny = std::max(plan.ny, layout.det_xyt[3 * i + 1] + 1);
+  }
+  const int32_t S = (int32_t)yx.size();
+  plan.S = S; plan.T = T;
+  plan.grid_site.assign((size_t)plan.nx * plan.ny, -1);
+  for (auto& q : yx) {
+    int32_t s = (int32_t)plan.site_x.size();
+    plan.site_x.push_back(q.second); plan.site_y.push_back(q.first);
+    plan.grid_site[(size_t)q.first * plan.nx + q.second] = s;
+  }
+  std::vector<int32_t> det_site(n_det), det_layer(n_det), det_at((size_t)S * T, -1);
+  for (int32_t i = 0; i < n_det; ++i) {
+    int32_t s = plan.grid_site[(size_t)layout.det_xyt[3 * i + 1] * plan.nx + layout.det_xyt[3 * i]];
+    int32_t t = layout.det_xyt[3 * i + 2];
+    det_site[i] = s; det_layer[i] = t;
+    if (det_at[(size_t)t * S + s] != -1) { err = "two detectors at one (site, layer)"; return TD_ERR_UNSUPPORTED; }
+    det_at[(size_t)t * S + s] = i;
+  }
+  if ((int64_t)S * T != n_det) { err = "every site needs exactly one detector in every layer"; return TD_ERR_UNSUPPORTED; }
+
+  // ---- merge identical mechanisms (Sec. 2.4) --------------------------------------------
+  std::map<std::pair<std::vector<int32_t>, int32_t>, int32_t> seen;
+  std::vector<Mech> mechs;
+  for (int32_t j = 0; j < n_mech; ++j) {
+    std::vector<int32_t> d = mdets[j];
+    std::sort(d.begin(), d.end());
+    auto key = std::make_pair(d, mobs[j]);
+    auto it = seen.find(key);
+    if (it != seen.end()) {
+      Mech& m = mechs[it->second];
+      m.p = m.p + dem.p[j] - 2 * m.p * dem.p[j];
+    } else {
+      seen[key] = (int32_t)mechs.size();
+      Mech m; m.dets = d; m.l = mobs[j]; m.p = dem.p[j];
+      mechs.push_back(m);
+    }
+  }
+
+  // ---- classify ----------------------------------------------------------------------------
+  for (Mech& m : mechs) {
+    if (m.dets.empty()) { m.kind = kGlobal; continue; }
+    if (m.dets.size() == 1) { m.kind = kSingle; m.a = det_site[m.dets[0]]; m.t = det_layer[m.dets[0]]; continue; }
+    if (m.dets.size() > 2) { err = "mechanism flips more than two detectors"; return TD_ERR_NONLOCAL; }
+    int32_t s0 = det_site[m.dets[0]], s1 = det_site[m.dets[1]];
+    int32_t t0 = det_layer[m.dets[0]], t1 = det_layer[m.dets[1]];
+    if (t0 == t1) {
+      int32_t dx = std::abs(plan.site_x[s0] - plan.site_x[s1]), dy = std::abs(plan.site_y[s0] - plan.site_y[s1]);
+      if (dx + dy != 1) { err = "two-detector mechanism between non-adjacent sites of one layer"; return TD_ERR_NONLOCAL; }
+      m.kind = kPair; m.a = std::min(s0, s1); m.b = std::max(s0, s1); m.t = t0;
+    } else if (s0 == s1 && std::abs(t0 - t1) == 1) {
+      m.kind = kVert; m.a = s0; m.t = std::min(t0, t1);
+    } else {
+      err = "two-detector mechanism that is neither in-layer nor vertical"; return TD_ERR_NONLOCAL;
+    }
+  }
+
+  // ---- class tracking: observable representative with fewer counter sites ----------------
+  auto counters_of = [&](bool deformed) {
+    std::set<int32_t> cs;
+    for (const Mech& m : mechs) {
+      int32_t l = m.l ^ ((deformed && m.kind == kSingle) ? 1 : 0);
+      if (!l) continue;
+      if (m.kind == kPair) cs.insert(m.a);
+      else if (m.kind == kSingle && m.t != T - 1) cs.insert(m.a);
+      else if (m.kind == kVert) cs.insert(m.a);
+    }
+    return cs;
+  };
+  std::set<int32_t> c0 = counters_of(false), c1 = counters_of(true);
+  bool deformed = c1.size() < c0.size();
+  std::set<int32_t>& cs = deformed ? c1 : c0;
+  plan.offset_all = deformed ? 1 : 0;
+  if (deformed)
+    for (Mech& m : mechs)
+      if (m.kind == kSingle) m.l ^= 1;
+  plan.P.assign(S, 2);
+  for (int32_t s : cs) plan.P[s] = 4;
+  plan.n_counter_sites = (int32_t)cs.size();
+  for (const Mech& m : mechs)
+    if (m.kind == kGlobal && m.l) {
+      double G[4] = {1 - m.p, m.p, m.p, 1 - m.p}, R[4];
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) R[i * 2 + j] = G[i * 2] * plan.glob_mix[j] + G[i * 2 + 1] * plan.glob_mix[2 + j];
+      std::memcpy(plan.glob_mix, R, sizeof(R));
+    }
+
+  // ---- bonds -------------------------------------------------------------------------------
+  std::map<std::pair<int32_t, int32_t>, int32_t> bond_of;
+  for (const Mech& m : mechs)
+    if (m.kind == kPair) bond_of[{m.a, m.b}] = 0;
+  for (auto& kv : bond_of) { kv.second = (int32_t)plan.bond_sites.size(); plan.bond_sites.push_back(kv.first); }
+  plan.n_bonds = (int32_t)plan.bond_sites.size();
+  std::vector<std::vector<int32_t>> site_bonds(S), site_dirs(S);
+  for (int32_t s = 0; s < S; ++s) {
+    const int32_t x = plan.site_x[s], y = plan.site_y[s];
+    const int32_t nbx[4] = {x - 1, x + 1, x, x}, nby[4] = {y, y, y - 1, y + 1};
+    for (int dir = 0; dir < 4; ++dir) {
+      if (nbx[dir] < 0 || nby[dir] < 0 || nbx[dir] >= plan.nx || nby[dir] >= plan.ny) continue;
+      int32_t o = plan.grid_site[(size_t)nby[dir] * plan.nx + nbx[dir]];
+      if (o < 0) continue;
+      auto it = bond_of.find({std::min(s, o), std::max(s, o)});
+      if (it == bond_of.end()) continue;
+      site_bonds[s].push_back(it->second);
+      site_dirs[s].push_back(dir);
+    }
+  }
+
+  // ---- per-layer local operators, gates, readout -------------------------------------------
+  std::vector<std::vector<const Mech*>> vert((size_t)T * S), read(S);
+  std::vector<double> pre((size_t)T * S * 16);
+  for (int32_t t = 0; t < T; ++t)
+    for (int32_t s = 0; s < S; ++s) eye(plan.P[s], &pre[((size_t)t * S + s) * 16]);
+  struct GateSpec { int colour, y, x; int32_t idx; const Mech* m; };
+  std::vector<std::vector<GateSpec>> layer_gates(T);
+  for (int32_t idx = 0; idx < (int32_t)mechs.size(); ++idx) {
+    const Mech& m = mechs[idx];
+    if (m.kind == kSingle) {
+      if (m.t == T - 1) { read[m.a].push_back(&m); continue; }
+      const int P = plan.P[m.a];
+      const int mask = 1 | (m.l ? 2 : 0);
+      double G[16];
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) G[i * P + j] = (i == j ? 1 - m.p : 0) + (i == (j ^ mask) ? m.p : 0);
+      double* A = &pre[((size_t)m.t * S + m.a) * 16];
+      matmul(P, G, A, A);
+    } else if (m.kind == kVert) {
+      vert[(size_t)m.t * S + m.a].push_back(&m);
+    } else if (m.kind == kPair) {
+      const int32_t xa = plan.site_x[m.a], ya = plan.site_y[m.a], xb = plan.site_x[m.b], yb = plan.site_y[m.b];
+      int colour = (ya == yb) ? (std::min(xa, xb) % 2) : 2 + (std::min(ya, yb) % 2);
+      layer_gates[m.t].push_back({colour, ya, xa, idx, &m});
+    }
+  }
+  auto post_matrix = [&](int32_t t, int32_t s, double* M) -> bool {   // vertical weights above layer t
+    const int P = plan.P[s];
+    double W[2][2];
+    parity_weights(vert[(size_t)t * S + s], W);
+    for (int i = 0; i < P * P; ++i) M[i] = 0;
+    for (int ph = 0; ph < P; ++ph) {
+      int tau = ph & 1, cl = ph >> 1;
+      for (int dc = 0; dc < 2; ++dc) {
+        if (W[tau][dc] == 0) continue;
+        if (P == 2 && dc) return false;
+        M[(tau | ((cl ^ dc) << 1)) * P + ph] += W[tau][dc];
+      }
+    }
+    return true;
+  };
+
+  // Static schedule: bond dims double per gate up to chi.  Pass 1 finds every site
+  // tensor's largest size, pass 2 assigns buffer offsets and emits descriptors.
+  std::vector<std::vector<std::vector<GateSpec>>> rounds_of(T);
+  for (int32_t t = 0; t < T; ++t) {
+    auto& g = layer_gates[t];
+    std::sort(g.begin(), g.end(), [](const GateSpec& a, const GateSpec& b) {
+      return std::tie(a.colour, a.y, a.x, a.idx) < std::tie(b.colour, b.y, b.x, b.idx);
+    });
+    for (int colour = 0; colour < 4; ++colour) {
+      std::vector<std::vector<GateSpec>> rr;
+      std::map<int32_t, int> count;
+      for (const GateSpec& gs : g) {
+        if (gs.colour != colour) continue;
+        int32_t b = bond_of[{gs.m->a, gs.m->b}];
+        int r = count[b]++;
+        if ((int)rr.size() <= r) rr.resize(r + 1);
+        rr[r].push_back(gs);
+      }
+      for (auto& r : rr) rounds_of[t].push_back(r);
+    }
+  }
+  auto site_size = [&](int32_t s, const std::vector<int32_t>& dims) {
+    int64_t n = plan.P[s];
+    for (int32_t b : site_bonds[s]) n *= dims[b];
+    return n;
+  };
+  std::vector<int64_t> maxsize(S);
+  {
+    std::vector<int32_t> dims(plan.n_bonds, 1);
+    for (int32_t s = 0; s < S; ++s) maxsize[s] = site_size(s, dims);
+    for (int32_t t = 0; t < T; ++t)
+      for (auto& r : rounds_of[t])
+        for (const GateSpec& gs : r) {
+          int32_t b = bond_of[{gs.m->a, gs.m->b}];
+          dims[b] = std::min(plan.chi, 2 * dims[b]);
+          maxsize[gs.m->a] = std::max(maxsize[gs.m->a], site_size(gs.m->a, dims));
+          maxsize[gs.m->b] = std::max(maxsize[gs.m->b], site_size(gs.m->b, dims));
+        }
+  }
+  std::vector<int64_t> base(S);
+  int64_t acc = 0;
+  for (int32_t s = 0; s < S; ++s) { base[s] = acc; acc += 2 * ((maxsize[s] + 3) / 4 * 4); }
+  plan.shot_elems = acc;
+  auto buf_off = [&](int32_t s, int k) { return base[s] + k * ((maxsize[s] + 3) / 4 * 4); };
+
+  std::vector<int32_t> dims(plan.n_bonds, 1), cur(S, 0);
+  plan.layers.resize(T);
+  for (int32_t t = 0; t < T; ++t) {
+    LayerPlan& L = plan.layers[t];
+    L.local_first = (int32_t)plan.locals.size();
+    for (int32_t s = 0; s < S; ++s) {
+      LocalDesc ld{};
+      ld.P = plan.P[s];
+      ld.det = det_at[(size_t)t * S + s];
+      ld.rest = (int32_t)(site_size(s, dims) / plan.P[s]);
+      ld.off = buf_off(s, cur[s]);
+      double K[16], post[16];
+      std::memcpy(K, &pre[((size_t)t * S + s) * 16], sizeof(K));
+      if (t > 0) {
+        if (!post_matrix(t - 1, s, post)) { err = "class-flipping vertical mechanism without counter"; return TD_ERR_INVALID; }
+        matmul(ld.P, K, post, K);
+      }
+      for (int i = 0; i < 16; ++i) ld.K[i] = i < ld.P * ld.P ? K[i] : 0.0;
+      plan.locals.push_back(ld);
+    }
+    for (auto& r : rounds_of[t]) {
+      Round R{};
+      R.first = (int32_t)plan.gates.size();
+      R.count = (int32_t)r.size();
+      for (const GateSpec& gs : r) {
+        GateDesc g{};
+        g.bond = bond_of[{gs.m->a, gs.m->b}];
+        g.D = dims[g.bond];
+        g.Dn = std::min(plan.chi, 2 * g.D);
+        g.p = gs.m->p;
+        const int32_t ends[2] = {gs.m->a, gs.m->b};
+        for (int side = 0; side < 2; ++side) {
+          SideDesc& sd = g.side[side];
+          const int32_t s = ends[side];
+          sd.site = s;
+          sd.P = plan.P[s];
+          sd.mask = 1 | ((side == 0 && gs.m->l) ? 2 : 0);
+          sd.nb = (int32_t)site_bonds[s].size();
+          sd.pos = -1;
+          sd.outer = 1; sd.inner = 1;
+          for (int k = 0; k < kMaxBonds; ++k) { sd.dims[k] = 1; sd.bond[k] = -1; }
+          for (int k = 0; k < sd.nb; ++k) {
+            sd.bond[k] = site_bonds[s][k];
+            sd.dims[k] = dims[site_bonds[s][k]];
+            if (site_bonds[s][k] == g.bond) sd.pos = k;
+          }
+          for (int k = 0; k < sd.nb; ++k) {
+            if (k < sd.pos) sd.outer *= sd.dims[k];
+            if (k > sd.pos) sd.inner *= sd.dims[k];
+          }
+          sd.in_off = buf_off(s, cur[s]);
+          sd.out_off = buf_off(s, cur[s] ^ 1);
+          R.max_rows = std::max(R.max_rows, sd.P / 2 * sd.outer * sd.inner);
+        }
+        R.maxD = std::max(R.maxD, g.D);
+        R.maxDn = std::max(R.maxDn, g.Dn);
+        dims[g.bond] = g.Dn;
+        cur[gs.m->a] ^= 1;
+        cur[gs.m->b] ^= 1;
+        plan.gates.push_back(g);
+      }
+      plan.max_round_gates = std::max(plan.max_round_gates, R.count);
+      L.rounds.push_back(R);
+    }
+  }
+  // readout of the last layer
+  for (int32_t s = 0; s < S; ++s) {
+    FinalSite f{};
+    f.P = plan.P[s];
+    f.nb = (int32_t)site_bonds[s].size();
+    for (int d = 0; d < 4; ++d) { f.dir_dim[d] = 1; f.dir_pos[d] = -1; f.dir_bond[d] = -1; }
+    for (int k = 0; k < f.nb; ++k) {
+      int d = site_dirs[s][k];
+      f.dir_pos[d] = k;
+      f.dir_bond[d] = site_bonds[s][k];
+      f.dir_dim[d] = dims[site_bonds[s][k]];
+    }
+    f.off = buf_off(s, cur[s]);
+    double W[2][2];
+    parity_weights(read[s], W);
+    for (int ph = 0; ph < f.P; ++ph) {
+      int tau = ph & 1, cl = ph >> 1;
+      for (int c = 0; c < 2; ++c) f.R[ph * 2 + c] = W[tau][c ^ cl];
+    }
+    plan.finals.push_back(f);
+  }
+  plan.final_dims = dims;
+  for (int32_t d : dims) plan.max_final_D = std::max(plan.max_final_D, d);
+  return TD_OK;
+}
+
+}  // namespace td

@@ -1,0 +1,64 @@
+// Kernel argument blocks and launchers of the sweep (sweep.cu) and the final contraction
+// (final.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "td_internal.h"
+
+namespace td {
+
+struct SweepArgs {
+  void* gamma;              // site tensors, [B][shot_elems] of the storage type
+  int64_t shot_elems;
+  double* lam;              // [B][nbonds][chi] bond weights
+  double* logacc;           // [B][nslots] log-scale accumulators (sites, bonds, final)
+  const uint8_t* det;       // [*][n_det] detector bits of the whole call
+  int32_t nbonds, chi, nslots, n_det;
+  int32_t wave_first;       // first shot of this wave in `det`
+  int32_t B;                // shots in this wave
+  double gram_cutoff, svd_cutoff, multiplet_rtol;
+};
+
+struct FinalArgs {
+  const void* gamma;
+  int64_t shot_elems;
+  const double* lam;
+  double* logacc;
+  const FinalSite* sites;
+  const int32_t* grid_site;  // [ny][nx]
+  void* scratch;             // [B][scratch_elems] of the accumulation type
+  double* Z;                 // [B][2]
+  int64_t scratch_elems;
+  int64_t off_mps0, off_mps1, mps_stride, off_C0, off_C1, off_F, off_T1, off_T, off_G, off_V, off_s;
+  int32_t nbonds, chi, nslots, slot;
+  int32_t nx, ny, chi_mps;
+  int32_t B;
+  double svd_cutoff, multiplet_rtol;
+};
+
+struct FinalizeArgs {
+  const double* Z;
+  const double* logacc;
+  const uint8_t* det;
+  double* logp;              // [*][2] or null
+  int32_t* decision;         // [*] or null
+  double* margin;            // [*] or null
+  int32_t nslots, n_det, wave_first, B, offset_all;
+  double mix[4];
+};
+
+template <typename T, typename R>
+cudaError_t launch_sweep_init(const SweepArgs& a, const LocalDesc* locals0, int S, cudaStream_t st);
+template <typename T, typename R>
+cudaError_t launch_local(const SweepArgs& a, const LocalDesc* locals, int S, cudaStream_t st);
+template <typename T, typename R>
+cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round& rd, void* gram, double* tbuf,
+                         double* t1buf, int S, cudaStream_t st);
+template <typename T, typename R>
+cudaError_t launch_final(const FinalArgs& f, cudaStream_t st);
+cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st);
+
+size_t core_smem_bytes(int D);
+
+}  // namespace td

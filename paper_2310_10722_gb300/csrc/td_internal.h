@@ -1,0 +1,109 @@
+// Internal data structures shared by the host planner and the CUDA kernels.
+//
+// The network plan is the layered detector network of Sec. 3.4 / Sec. 4 for a graph-like
+// DEM: sites are the (x, y) positions of one layer, the boundary state is a PEPS with one
+// physical leg per site (the bit of the vertical mechanism entering the layer, plus a class
+// counter bit on counter sites), and each layer is absorbed as site-local matrices and
+// two-site gates (1-p) I x I + p X x X on grid bonds, each followed by a simple-update
+// truncation of its bond to chi.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/td.h"
+
+namespace td {
+
+constexpr int kMaxChi = 32;      // simple-update bond cap supported by the kernels
+constexpr int kMaxBonds = 4;     // grid sites have at most 4 bonds
+constexpr int kMaxPhys = 4;      // physical leg: vertical bit x class counter bit
+
+// One endpoint of a gate: the site tensor is stored as [phys][d_0]...[d_{nb-1}] (row
+// major, bonds ordered left, right, down, up) and viewed as [phys][outer][D][inner]
+// around the active bond at position `pos`.
+struct SideDesc {
+  int32_t site;
+  int32_t P;            // physical dimension (2 or 4)
+  int32_t mask;         // physical index flip of the gate's X on this side (1 or 3)
+  int32_t nb;           // bonds of the site
+  int32_t pos;          // position of the active bond
+  int32_t dims[kMaxBonds];   // current bond dimensions (before the gate)
+  int32_t bond[kMaxBonds];   // global bond ids (lambda lookup)
+  int32_t outer, inner; // product of dims before / after `pos`
+  int64_t in_off;       // element offset of the current tensor in a shot block
+  int64_t out_off;      // element offset of the updated tensor in a shot block
+};
+
+struct GateDesc {
+  SideDesc side[2];
+  int32_t bond;
+  int32_t D, Dn;        // active bond dimension before / after
+  double p;             // mechanism probability
+};
+
+// Site-local operator applied at the start of a layer: psi <- X^{m} K psi on the
+// physical leg (K = this layer's single-detector mechanisms times the previous layer's
+// vertical weights), then rescaled by its largest magnitude.
+struct LocalDesc {
+  int32_t P;
+  int32_t det;          // detector index of (site, layer): its bit flips phys bit 0
+  int32_t rest;         // product of the site's current bond dims
+  int32_t pad;
+  int64_t off;          // element offset of the current tensor in a shot block
+  double K[kMaxPhys * kMaxPhys];
+};
+
+// Final readout of one site for the 2D contraction: F[c][l][r][d][u] =
+// sum_phys R[phys][c] Gamma[phys][bonds] * prod sqrt(lambda).
+struct FinalSite {
+  int32_t P;
+  int32_t nb;
+  int32_t dir_dim[4];   // dimension per direction (left, right, down, up); 1 if absent
+  int32_t dir_pos[4];   // position of that direction's bond in the site tensor, -1 if absent
+  int32_t dir_bond[4];  // global bond id per direction, -1 if absent
+  int64_t off;          // element offset of the final tensor in a shot block
+  double R[kMaxPhys * 2];
+};
+
+struct Round {             // gates on disjoint bonds, run as one batch
+  int32_t first, count;    // range in the gate descriptor array
+  int32_t maxD, maxDn;
+  int32_t max_rows;        // max over sides of (P/2) * outer * inner
+};
+
+struct LayerPlan {
+  int32_t local_first;     // S local descriptors
+  std::vector<Round> rounds;
+};
+
+struct Plan {
+  int32_t n_det = 0, n_mech = 0, n_obs = 0;
+  int32_t nx = 0, ny = 0, T = 0, S = 0;
+  int32_t chi = 8, chi_mps = 16, precision = TD_FP64;
+  double svd_cutoff = 1e-12, multiplet_rtol = 1e-8, gram_cutoff = 1e-13;
+  std::vector<int32_t> site_x, site_y;
+  std::vector<int32_t> grid_site;        // [ny*nx] -> site or -1
+  std::vector<int32_t> P;                // per site
+  int32_t n_counter_sites = 0;
+  int32_t offset_all = 0;                // class offset = parity of all detector bits
+  double glob_mix[4] = {1, 0, 0, 1};     // class mixing by mechanisms with no detectors
+  std::vector<std::pair<int32_t, int32_t>> bond_sites;
+  int32_t n_bonds = 0;
+  std::vector<GateDesc> gates;
+  std::vector<LocalDesc> locals;
+  std::vector<LayerPlan> layers;
+  std::vector<FinalSite> finals;
+  std::vector<int32_t> final_dims;       // per bond, dimension after the sweep
+  int64_t shot_elems = 0;                // PEPS elements per shot (both buffers of all sites)
+  int32_t max_round_gates = 0;
+  int32_t max_final_D = 1;               // largest bond after the sweep
+};
+
+// Build the plan from the ABI structures.  Returns TD_OK or an error with `err` set.
+td_status build_plan(const td_dem& dem, const td_layout& layout, const td_options& opt, Plan& plan,
+                     std::string& err);
+
+}  // namespace td
