@@ -155,6 +155,27 @@ td_status td_network_get_info(const td_network* net, td_network_info* info);
 td_status td_debug_sweep(td_network* net, const uint8_t* det_dev, int64_t B, int32_t n_gates, double* lam_dev,
                          double* logacc_dev, int32_t* applied, void* stream);
 
+/* Kernel classes timed by td_network_profile. */
+typedef enum {
+  TD_K_INIT = 0, TD_K_LOCAL = 1, TD_K_GRAM = 2, TD_K_PRE = 3, TD_K_CORE = 4, TD_K_UPDATE = 5,
+  TD_K_FINAL = 6, TD_K_FINALIZE = 7, TD_K_COUNT = 8
+} td_kernel_class;
+
+/* Kernel timing with CUDA events recorded on the call's stream around every launch.
+ * enable = 1 starts recording (and clears earlier records), 0 stops.  With ms and
+ * launches non-NULL (arrays of TD_K_COUNT), synchronises the recorded events and writes,
+ * per kernel class, the summed device time in milliseconds and the number of launches
+ * since recording started. */
+td_status td_network_profile(td_network* net, int32_t enable, double* ms, int64_t* launches);
+
+/* Algorithmic work per shot of one decoding call, per kernel class (arrays of TD_K_COUNT),
+ * from the network's static bond dimensions (an upper bound where truncation keeps fewer):
+ * bytes = minimum device-memory traffic (each tensor a kernel must read or write, once);
+ * flops = multiply-adds x 2 of the contractions, plus textbook counts for the dense
+ * factorisations (symmetric eigensolver with vectors 9n^3; SVD of m x n, m >= n, with both
+ * factors 4m^2 n + 8m n^2 + 9n^3).  fp64_flops = the part of flops done in FP64. */
+td_status td_network_get_work(const td_network* net, double* bytes, double* flops, double* fp64_flops);
+
 /* Release the network and its device workspace (NULL is a no-op).  The caller must
  * ensure no enqueued work still uses it. */
 void td_free_network(td_network* net);

@@ -149,6 +149,21 @@ class Network:
                                        C.c_void_p(la.data_ptr()), C.byref(applied), self._stream(stream)))
         return lam, la, applied.value
 
+    def profile(self, enable: bool):
+        """Start (True) or stop (False) per-launch CUDA-event timing; returns the totals
+        recorded so far as {kernel class: (ms, launches)}."""
+        ms = (C.c_double * 8)()
+        n = (C.c_int64 * 8)()
+        check(self._lib.td_network_profile(self._h, int(enable), C.cast(ms, C.c_void_p), C.cast(n, C.c_void_p)))
+        return {k: (ms[i], n[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)}
+
+    def work(self) -> dict:
+        """Algorithmic work per shot per kernel class: {class: (bytes, flops, fp64_flops)}."""
+        b, f, f64 = (C.c_double * 8)(), (C.c_double * 8)(), (C.c_double * 8)()
+        check(self._lib.td_network_get_work(self._h, C.cast(b, C.c_void_p), C.cast(f, C.c_void_p),
+                                            C.cast(f64, C.c_void_p)))
+        return {k: (b[i], f[i], f64[i]) for i, k in enumerate(_lib.KERNEL_CLASSES)}
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.td_free_network(self._h)

@@ -49,10 +49,32 @@ struct td_network {
   size_t bytes = 0;
   int64_t launches_per_wave = 0;
   std::vector<void*> allocs;
+  // kernel timing (td_network_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
 
   ~td_network() {
     for (void* p : allocs) cudaFree(p);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (auto& u : ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
   }
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) { cudaEvent_t e = ev_pool.back(); ev_pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Brackets one launch of kernel class k with events when profiling.
+  struct Mark {
+    td_network* n; int k; cudaStream_t s; cudaEvent_t a = nullptr;
+    Mark(td_network* net, int cls, cudaStream_t st) : n(net), k(cls), s(st) {
+      if (n->profiling) { a = n->take_event(); cudaEventRecord(a, s); }
+    }
+    ~Mark() {
+      if (a) { cudaEvent_t b = n->take_event(); cudaEventRecord(b, s); n->ev_used.push_back({k, {a, b}}); }
+    }
+  };
   template <typename P>
   bool alloc(P*& ptr, size_t n) {
     void* p = nullptr;
@@ -173,9 +195,19 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   return TD_OK;
 }
 
+struct NetProf : td::Prof {
+  td_network* n; cudaStream_t s; cudaEvent_t a = nullptr;
+  NetProf(td_network* net, cudaStream_t st) : n(net), s(st) {}
+  void begin(int) override { if (n->profiling) { a = n->take_event(); cudaEventRecord(a, s); } }
+  void end(int k) override {
+    if (a) { cudaEvent_t b = n->take_event(); cudaEventRecord(b, s); n->ev_used.push_back({k, {a, b}}); a = nullptr; }
+  }
+};
+
 static td_status run(td_network* net, const uint8_t* det, int64_t B, double* logp, int32_t* decision, double* margin,
                      cudaStream_t st) {
   td::Plan& P = net->plan;
+  NetProf prof(net, st);
   for (int64_t w0 = 0; w0 < B; w0 += net->wave) {
     const int32_t Bw = (int32_t)std::min<int64_t>(net->wave, B - w0);
     td::SweepArgs a{};
@@ -194,17 +226,25 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     a.svd_cutoff = P.svd_cutoff;
     a.multiplet_rtol = P.multiplet_rtol;
     const bool f64 = P.precision == TD_FP64;
-    cudaError_t e = f64 ? td::launch_sweep_init<double, double>(a, net->d_locals, P.S, st)
-                        : td::launch_sweep_init<float, float>(a, net->d_locals, P.S, st);
+    cudaError_t e;
+    {
+      td_network::Mark mk(net, TD_K_INIT, st);
+      e = f64 ? td::launch_sweep_init<double, double>(a, net->d_locals, P.S, st)
+              : td::launch_sweep_init<float, float>(a, net->d_locals, P.S, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "init launch");
     for (int32_t t = 0; t < P.T; ++t) {
       const td::LayerPlan& L = P.layers[t];
-      e = f64 ? td::launch_local<double, double>(a, net->d_locals + L.local_first, P.S, st)
-              : td::launch_local<float, float>(a, net->d_locals + L.local_first, P.S, st);
+      {
+        td_network::Mark mk(net, TD_K_LOCAL, st);
+        e = f64 ? td::launch_local<double, double>(a, net->d_locals + L.local_first, P.S, st)
+                : td::launch_local<float, float>(a, net->d_locals + L.local_first, P.S, st);
+      }
       if (e != cudaSuccess) return cuda_fail(e, "local launch");
       for (const td::Round& rd : L.rounds) {
-        e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, nullptr, P.S, st)
-                : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, net->d_t1buf, P.S, st);
+        e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, nullptr, P.S, st, &prof)
+                : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, net->d_t1buf, P.S, st,
+                                                 &prof);
         if (e != cudaSuccess) return cuda_fail(e, "gate round launch");
       }
     }
@@ -227,7 +267,10 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     f.B = Bw;
     f.svd_cutoff = P.svd_cutoff;
     f.multiplet_rtol = P.multiplet_rtol;
-    e = f64 ? td::launch_final<double, double>(f, st) : td::launch_final<float, float>(f, st);
+    {
+      td_network::Mark mk(net, TD_K_FINAL, st);
+      e = f64 ? td::launch_final<double, double>(f, st) : td::launch_final<float, float>(f, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "final launch");
     td::FinalizeArgs z{};
     z.Z = net->d_Z;
@@ -242,7 +285,10 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     z.B = Bw;
     z.offset_all = P.offset_all;
     for (int i = 0; i < 4; ++i) z.mix[i] = P.glob_mix[i];
-    e = td::launch_finalize(z, st);
+    {
+      td_network::Mark mk(net, TD_K_FINALIZE, st);
+      e = td::launch_finalize(z, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "finalize launch");
   }
   return TD_OK;
@@ -361,6 +407,105 @@ td_status td_network_get_info(const td_network* net, td_network_info* info) {
   info->offset_all = P.offset_all;
   info->workspace_bytes = net->bytes;
   info->launches_per_wave = net->launches_per_wave;
+  return TD_OK;
+}
+
+td_status td_network_get_work(const td_network* net, double* bytes, double* flops, double* fp64_flops) {
+  g_err.clear();
+  if (!net || !bytes || !flops || !fp64_flops) return fail(TD_ERR_INVALID, "null argument");
+  const td::Plan& P = net->plan;
+  const double el = (double)net->elem;
+  const bool f64 = P.precision == TD_FP64;
+  for (int k = 0; k < TD_K_COUNT; ++k) { bytes[k] = 0; flops[k] = 0; fp64_flops[k] = 0; }
+  auto eig = [](double n) { return 9.0 * n * n * n; };
+  auto svd = [](double m, double n) {
+    if (m < n) std::swap(m, n);
+    return 4.0 * m * m * n + 8.0 * m * n * n + 9.0 * n * n * n;
+  };
+  bytes[TD_K_INIT] = 0;
+  for (const td::LocalDesc& d : P.locals) {
+    bytes[TD_K_LOCAL] += 2.0 * d.P * d.rest * el;
+    flops[TD_K_LOCAL] += 2.0 * d.P * d.P * d.rest;
+  }
+  for (const td::GateDesc& g : P.gates) {
+    const double D = g.D, Dn = g.Dn;
+    for (int s = 0; s < 2; ++s) {
+      const td::SideDesc& sd = g.side[s];
+      const double OI = (double)sd.outer * sd.inner;
+      const double rows = sd.P / 2 * OI;
+      const double in = sd.P * OI * D * el, out = sd.P * OI * Dn * el;
+      const int passes = f64 ? 1 : 2;
+      bytes[TD_K_GRAM] += passes * in;
+      flops[TD_K_GRAM] += passes * 2.0 * rows * 2.0 * D * D + (f64 ? 0.0 : 2.0 * rows * 2.0 * D * D);
+      if (f64) fp64_flops[TD_K_GRAM] += 2.0 * rows * 2.0 * D * D;
+      bytes[TD_K_UPDATE] += in + out;
+      flops[TD_K_UPDATE] += 2.0 * rows * 2.0 * D * Dn;
+      if (f64) fp64_flops[TD_K_UPDATE] += 2.0 * rows * 2.0 * D * Dn;
+    }
+    if (!f64) {
+      flops[TD_K_PRE] += 4.0 * eig(D);
+      fp64_flops[TD_K_PRE] += 4.0 * eig(D);
+    }
+    const double core = 4.0 * eig(D) + svd(2 * D, 2 * D) + 2.0 * 4.0 * D * D * D + 2.0 * 4.0 * D * Dn * 2 * D;
+    flops[TD_K_CORE] += core;
+    fp64_flops[TD_K_CORE] += core;
+    bytes[TD_K_CORE] += 4.0 * D * D * (f64 ? 8 : 4) + 4.0 * D * Dn * 8;
+  }
+  // final contraction: zip-up with static dims, kept bond min(chi_mps, m, n) at every cut
+  std::vector<double> mL(P.nx, 1), mDn(P.nx, 1), mR(P.nx, 1);
+  mR[P.nx - 1] = 2;
+  for (int y = 0; y < P.ny; ++y) {
+    double cJ = 1;
+    std::vector<double> nL(P.nx), nD(P.nx), nR(P.nx);
+    for (int x = 0; x < P.nx; ++x) {
+      const int s = P.grid_site[(size_t)y * P.nx + x];
+      double L = 1, R = 1, Dd = 1, U = 1;
+      if (s >= 0) {
+        const td::FinalSite& f = P.finals[s];
+        L = f.dir_dim[0]; R = f.dir_dim[1]; Dd = f.dir_dim[2]; U = f.dir_dim[3];
+        double rest = L * R * Dd * U;
+        bytes[TD_K_FINAL] += f.P * rest * el;
+      }
+      const double aL = mL[x], aD = mDn[x], aR = mR[x];
+      flops[TD_K_FINAL] += 2.0 * cJ * L * 2 * aD * aR * aL + 2.0 * cJ * U * aR * R * 2 * (L * 2 * aD);
+      const double m = cJ * U, n = aR * R * 2;
+      if (x < P.nx - 1 && y < P.ny - 1) {
+        flops[TD_K_FINAL] += svd(m, n);
+        const double k = std::min<double>(P.chi_mps, std::min(m, n));
+        nL[x] = cJ; nD[x] = U; nR[x] = k;
+        cJ = k;
+      } else if (x < P.nx - 1) {
+        nL[x] = cJ; nD[x] = U; nR[x] = m;
+        cJ = m;
+      } else {
+        nL[x] = cJ; nD[x] = U; nR[x] = 2;
+      }
+    }
+    mL = nL; mDn = nD; mR = nR;
+  }
+  if (f64) fp64_flops[TD_K_FINAL] = flops[TD_K_FINAL];
+  bytes[TD_K_FINALIZE] = (double)net->nslots * 8 + P.n_det + 16;
+  return TD_OK;
+}
+
+td_status td_network_profile(td_network* net, int32_t enable, double* ms, int64_t* launches) {
+  g_err.clear();
+  if (!net) return fail(TD_ERR_INVALID, "null network");
+  if (ms && launches) {
+    for (int k = 0; k < TD_K_COUNT; ++k) { ms[k] = 0; launches[k] = 0; }
+    for (auto& u : net->ev_used) {
+      cudaError_t e = cudaEventSynchronize(u.second.second);
+      if (e != cudaSuccess) return cuda_fail(e, "profile event");
+      float t = 0;
+      e = cudaEventElapsedTime(&t, u.second.first, u.second.second);
+      if (e != cudaSuccess) return cuda_fail(e, "profile elapsed");
+      ms[u.first] += t;
+      launches[u.first] += 1;
+    }
+  }
+  for (auto& u : net->ev_used) { net->ev_pool.push_back(u.second.first); net->ev_pool.push_back(u.second.second); }
+  net->ev_used.clear();
+  net->profiling = enable != 0;
   return TD_OK;
 }
 

@@ -523,12 +523,16 @@ size_t core_smem_bytes(int D) {
 
 template <typename T, typename R>
 cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round& rd, void* gram, double* tbuf,
-                         double* t1buf, int S, cudaStream_t st) {
+                         double* t1buf, int S, cudaStream_t st, Prof* prof) {
   const GateDesc* g = gates + rd.first;
   const int D = rd.maxD, Dn = rd.maxDn;
   const size_t smem_g = sizeof(R) * (4 * kGramRows * D + 2 * D * D + kGramRows + 2) +
                         sizeof(double) * (kMaxBonds * a.chi + 1) + 16;
+  auto B = [&](int k) { if (prof) prof->begin(k); };
+  auto E = [&](int k) { if (prof) prof->end(k); };
+  B(TD_K_GRAM);
   k_gram<T, R><<<dim3(2 * rd.count, a.B), 256, smem_g, st>>>(a, g, reinterpret_cast<R*>(gram), nullptr);
+  E(TD_K_GRAM);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool refine = t1buf != nullptr;
@@ -538,10 +542,14 @@ cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round&
       e = cudaFuncSetAttribute(k_pre<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
       if (e != cudaSuccess) return e;
     }
+    B(TD_K_PRE);
     k_pre<R><<<dim3(rd.count, a.B), 128, smem_p, st>>>(a, g, reinterpret_cast<const R*>(gram), t1buf);
+    E(TD_K_PRE);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    B(TD_K_GRAM);
     k_gram<T, R><<<dim3(2 * rd.count, a.B), 256, smem_g, st>>>(a, g, reinterpret_cast<R*>(gram), t1buf);
+    E(TD_K_GRAM);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -550,12 +558,16 @@ cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round&
     e = cudaFuncSetAttribute(k_core<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
     if (e != cudaSuccess) return e;
   }
+  B(TD_K_CORE);
   k_core<R><<<dim3(rd.count, a.B), 128, smem_c, st>>>(a, g, reinterpret_cast<const R*>(gram), tbuf, S, t1buf);
+  E(TD_K_CORE);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int tiles = (rd.max_rows + kUpdRows - 1) / kUpdRows;
   const size_t smem_u = sizeof(R) * (2 * D * Dn + 2 * kUpdRows * D);
+  B(TD_K_UPDATE);
   k_update<T, R><<<dim3(2 * rd.count * tiles, a.B), 256, smem_u, st>>>(a, g, tbuf, tiles);
+  E(TD_K_UPDATE);
   return cudaGetLastError();
 }
 
@@ -564,8 +576,8 @@ template cudaError_t launch_sweep_init<float, float>(const SweepArgs&, const Loc
 template cudaError_t launch_local<double, double>(const SweepArgs&, const LocalDesc*, int, cudaStream_t);
 template cudaError_t launch_local<float, float>(const SweepArgs&, const LocalDesc*, int, cudaStream_t);
 template cudaError_t launch_round<double, double>(const SweepArgs&, const GateDesc*, const Round&, void*, double*,
-                                                  double*, int, cudaStream_t);
+                                                  double*, int, cudaStream_t, Prof*);
 template cudaError_t launch_round<float, float>(const SweepArgs&, const GateDesc*, const Round&, void*, double*,
-                                                double*, int, cudaStream_t);
+                                                double*, int, cudaStream_t, Prof*);
 
 }  // namespace td

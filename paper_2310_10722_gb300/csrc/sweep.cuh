@@ -48,13 +48,20 @@ struct FinalizeArgs {
   double mix[4];
 };
 
+// Optional timing hooks around each kernel launch (kernel class ids of td_kernel_class).
+struct Prof {
+  virtual void begin(int k) = 0;
+  virtual void end(int k) = 0;
+  virtual ~Prof() {}
+};
+
 template <typename T, typename R>
 cudaError_t launch_sweep_init(const SweepArgs& a, const LocalDesc* locals0, int S, cudaStream_t st);
 template <typename T, typename R>
 cudaError_t launch_local(const SweepArgs& a, const LocalDesc* locals, int S, cudaStream_t st);
 template <typename T, typename R>
 cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round& rd, void* gram, double* tbuf,
-                         double* t1buf, int S, cudaStream_t st);
+                         double* t1buf, int S, cudaStream_t st, Prof* prof = nullptr);
 template <typename T, typename R>
 cudaError_t launch_final(const FinalArgs& f, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st);
