@@ -135,6 +135,22 @@ td_status td_decode(td_network* net, const uint8_t* det_dev, int64_t B, int32_t*
 td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_t B,
                                 double* logp_host, void* stream);
 
+/* td_coset_logprob for callers that cannot call cudaMalloc or cudaFree around a decode --
+ * for example code that runs where device memory is fixed up front and no allocator may be
+ * called.  This call allocates nothing: the scratch of the final 2D contraction is a
+ * file-scope static device array of 64 MiB instead of the network's workspace (the paper
+ * has no counterpart; it is a property of this library).  Arguments and results are those
+ * of td_coset_logprob.  B may not exceed min(wave, 64 MiB / final-contraction scratch per
+ * shot); a larger B returns TD_ERR_INVALID with the capacity in td_last_error().
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.  Every call
+ * on a device shares the one array and leaves its contents behind (nothing in it needs to
+ * start at zero): calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads -- race on it and must be serialised by the caller.  Every GPU that
+ * loads the library holds the array until the process exits. */
+td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
+                                  void* stream);
+
 /* Gradient of the mean total log-probability (1/B) sum_b log P(m_b), P(m) = sum_L p_{m,L},
  * with respect to every mechanism rate (the adjoint of the Sec. 4 sweep).  p_dev: device
  * double [n_mech] rates to use (NULL: the build rates); logP_dev: device double [B];

@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NONLOCAL", 3: "TD_ER
 
 EXPORTS = ["td_default_options", "td_build_network", "td_coset_logprob", "td_decode",
            "td_coset_logprob_host", "td_grad_logprob", "td_network_get_info", "td_debug_sweep",
-           "td_network_profile", "td_network_get_work", "td_free_network",
+           "td_network_profile", "td_network_get_work", "td_coset_logprob_static", "td_free_network",
            "td_last_error"]
 
 
@@ -81,6 +81,8 @@ def load(path: str | None = None):
     lib.td_network_profile.restype = C.c_int
     lib.td_network_get_work.argtypes = [vp, vp, vp, vp]
     lib.td_network_get_work.restype = C.c_int
+    lib.td_coset_logprob_static.argtypes = [vp, vp, C.c_int64, vp, vp]
+    lib.td_coset_logprob_static.restype = C.c_int
     lib.td_free_network.argtypes = [vp]
     lib.td_free_network.restype = None
     lib.td_last_error.argtypes = []

@@ -205,7 +205,7 @@ struct NetProf : td::Prof {
 };
 
 static td_status run(td_network* net, const uint8_t* det, int64_t B, double* logp, int32_t* decision, double* margin,
-                     cudaStream_t st) {
+                     cudaStream_t st, void* final_scratch = nullptr) {
   td::Plan& P = net->plan;
   NetProf prof(net, st);
   for (int64_t w0 = 0; w0 < B; w0 += net->wave) {
@@ -255,7 +255,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     f.logacc = net->d_logacc;
     f.sites = net->d_finals;
     f.grid_site = net->d_grid;
-    f.scratch = net->d_fscr;
+    f.scratch = final_scratch ? final_scratch : net->d_fscr;
     f.Z = net->d_Z;
     f.nbonds = P.n_bonds;
     f.chi = P.chi;
@@ -340,6 +340,27 @@ td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
   return TD_OK;
+}
+
+td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
+                                  void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (B > 0 && !logp_dev) return fail(TD_ERR_INVALID, "null output buffer");
+  const size_t per_shot = (size_t)net->fin.scratch_elems * net->elem;
+  const int64_t cap = (int64_t)std::min<size_t>(td::kStaticFinalScratchBytes / std::max<size_t>(per_shot, 1),
+                                                (size_t)net->wave);
+  if (B > cap)
+    return fail(TD_ERR_INVALID, "B = " + std::to_string(B) + " exceeds the static scratch capacity of this network: " +
+                                    std::to_string(cap) + " shots (" + std::to_string(per_shot) +
+                                    " bytes of final-contraction scratch per shot in a " +
+                                    std::to_string(td::kStaticFinalScratchBytes >> 20) + " MiB array)");
+  if (B == 0) return TD_OK;
+  void* scr = nullptr;
+  cudaError_t e = td::static_final_scratch(&scr);
+  if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");
+  return run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream), scr);
 }
 
 td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev, double* logP_dev,

@@ -9,6 +9,7 @@
 // each row into a two-valued output leg of the last MPS tensor.  The last row is contracted
 // exactly.
 #include <cmath>
+#include <mutex>
 
 #include "linalg.cuh"
 #include "sweep.cuh"
@@ -301,6 +302,34 @@ cudaError_t launch_final(const FinalArgs& f, cudaStream_t st) {
 cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st) {
   k_finalize<<<(f.B + 127) / 128, 128, 0, st>>>(f);
   return cudaGetLastError();
+}
+
+// ---- final contraction with scratch in a static device array ----------------------------
+// For callers that cannot call cudaMalloc: the scratch of k_final comes from this
+// file-scope array instead of the network workspace.  Every GPU that loads the library holds
+// it until the process exits.  Host code must not use the symbol as an address; the device
+// address is looked up once per device (cudaGetSymbolAddress) with that device current.
+static __device__ __align__(256) unsigned char g_final_scratch[kStaticFinalScratchBytes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxStaticDevices] = {};
+}  // namespace
+
+cudaError_t static_final_scratch(void** ptr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxStaticDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_final_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = p;
+  }
+  *ptr = g_static_ptr[dev];
+  return cudaSuccess;
 }
 
 template cudaError_t launch_final<double, double>(const FinalArgs&, cudaStream_t);

@@ -68,4 +68,10 @@ cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st);
 
 size_t core_smem_bytes(int D);
 
+// Static scratch of the allocation-free final contraction (final.cu).
+constexpr size_t kStaticFinalScratchBytes = size_t(64) << 20;   // 64 MiB
+constexpr int kMaxStaticDevices = 64;
+// Device address of the static scratch on the current device (looked up on first use).
+cudaError_t static_final_scratch(void** ptr);
+
 }  // namespace td
