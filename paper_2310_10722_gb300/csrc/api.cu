@@ -127,27 +127,41 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   net->elem = (o.precision == TD_FP64) ? 8 : 4;
   net->nslots = P.S + P.n_bonds + 1;
 
-  // final-contraction scratch per shot (elements of the accumulation type)
+  // final-contraction scratch per shot (elements of the accumulation type): the boundary
+  // MPS (two buffers) in global memory, and the work region of one block -- in shared
+  // memory when it fits, otherwise after the MPS in global memory
   const int64_t cmx = std::max(cm, 2);
   const int64_t mps_stride = ((int64_t)cm * Dm * cmx + 3) / 4 * 4;
-  const int64_t mC = (int64_t)cm * cmx * Dm * 2 + 4;
-  const int64_t mF = 2LL * Dm * Dm * Dm * Dm + 4;
-  const int64_t mT1 = (int64_t)cm * Dm * 2 * Dm * cmx + 4;
-  const int64_t mT = (int64_t)cm * Dm * cmx * Dm * 2 + (int64_t)cm * Dm + 8;   // + ordering scratch
-  const int64_t mG = (int64_t)cm * Dm * cmx * Dm * 2 + 4;      // M^T, n x m
+  const int64_t mF = 2LL * Dm * Dm * Dm * Dm;
+  const int64_t mW = std::max<int64_t>((int64_t)cm * Dm * 2 * Dm * cmx, (int64_t)cm * Dm * (cm * Dm + 1));
+  const int64_t mMT = (int64_t)cm * Dm * (cmx * Dm * 2 + 1);
+  const int64_t mC = (int64_t)cm * cmx * Dm * 2;
+  const int64_t mS = 2LL * cm * Dm;
+  const int64_t mOrd = ((int64_t)cm * Dm * 4 + net->elem - 1) / net->elem;
+  int64_t wacc = 0;
+  auto wtake = [&](int64_t n) { int64_t r = wacc; wacc += (n + 3) / 4 * 4; return r; };
+  net->fin.w_F = wtake(mF);
+  net->fin.w_W = wtake(mW);
+  net->fin.w_MT = wtake(mMT);
+  net->fin.w_C0 = wtake(mC);
+  net->fin.w_C1 = wtake(mC);
+  net->fin.w_s = wtake(mS);
+  net->fin.w_ord = wtake(mOrd);
+  net->fin.work_elems = wacc;
+  int smem_optin = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    smem_optin = 0;
+  }
+  const size_t static_smem = 8 * 1024;   // k_final's own shared arrays
+  net->fin.use_smem = ((size_t)wacc * net->elem + static_smem <= (size_t)smem_optin) ? 1 : 0;
   int64_t acc = 0;
   auto take = [&](int64_t n) { int64_t r = acc; acc += (n + 3) / 4 * 4; return r; };
   net->fin.off_mps0 = take(mps_stride * P.nx);
   net->fin.off_mps1 = take(mps_stride * P.nx);
   net->fin.mps_stride = mps_stride;
-  net->fin.off_C0 = take(mC);
-  net->fin.off_C1 = take(mC);
-  net->fin.off_F = take(mF);
-  net->fin.off_T1 = take(mT1);
-  net->fin.off_T = take(mT);
-  net->fin.off_G = take(mG);
-  net->fin.off_V = take((int64_t)cm * Dm * cm * Dm + 4);
-  net->fin.off_s = take(2 * (int64_t)cm * Dm + 4);
+  net->fin.off_work = net->fin.use_smem ? 0 : take(wacc);
   net->fin.scratch_elems = acc;
 
   const size_t per_shot = P.shot_elems * net->elem + (size_t)P.n_bonds * chi * 8 + (size_t)net->nslots * 8 +
@@ -184,9 +198,6 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
     delete net;
     return cuda_fail(e, "descriptor upload");
   }
-  // kernels need > 48 KiB of dynamic shared memory for chi > 16
-  const size_t smem_c = td::core_smem_bytes(chi);
-  (void)smem_c;
   int64_t launches = 1 + 2;   // init, final, finalize
   const int per_round = (o.precision == TD_FP64) ? 3 : 5;
   for (const td::LayerPlan& L : P.layers) launches += 1 + per_round * (int64_t)L.rounds.size();

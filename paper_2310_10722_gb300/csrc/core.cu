@@ -1,0 +1,413 @@
+// Simple-update truncation core of one gate (Sec. 4), one team of threads per (gate, shot).
+//
+// Input: the four Gram blocks G_{X,kappa} (X = A, B; kappa = +, -) of the two sides'
+// matrices in the kappa basis of the doubled bond (see sweep.cu).  A pivoted Cholesky
+// factor R of each block (G = R^T R, rank-revealing) is an R factor of that side's QR
+// decomposition, so the two-site core of the simple update is
+//     theta = [c(ka, kb) R_{A ka} Lambda R_{B kb}^T],  c(+,+) = c(-,-) = 1/2,
+//     c(+,-) = c(-,+) = (1 - 2p)/2,
+// a (rA x rB) matrix, rA, rB <= 2D.  Its SVD theta = U S V^T is truncated to k <= chi values
+// (cutoff and multiplet rule), the bond weight becomes S/s_1 (ln s_1 to the log-scale) and
+// the update transforms T_{X kappa} = R_{X kappa}^+ [U or V]_{kappa rows, :k} / sqrt2 are
+// written for k_update.
+//
+// FP32 storage refines the R factors once (an eigen-free CholeskyQR2 with a shift): k_pre
+// factors the first FP32 Gram plus a shift of kPreFloor of the side's largest diagonal,
+// R1, and emits T1 = R1^-1 and R1; k_gram then forms the Gram of Q1 = M T1, whose pivoted
+// Cholesky R2 gives R = R2 R1 and R^+ = T1 R2^+.
+//
+// The SVD of theta is FP64 one-sided Jacobi.  With `precond` (the mixed-precision path) it
+// is first solved in FP32 on a scaled copy; the FP32 right factor, re-orthogonalised in
+// FP64 by one Newton-Schulz step V <- V (3I - V^T V)/2, preconditions the FP64 Jacobi
+// sweeps, which then converge in one or two sweeps (mixed-precision Jacobi: precondition
+// with a low-precision factor, finish in high precision).
+#include <cfloat>
+#include <cmath>
+
+#include "sweep.cuh"
+#include "team.cuh"
+
+namespace td {
+
+constexpr double kPreFloor = 1e-6;
+
+// Team-shared layout of one item (doubles): five regions of regsz(Dm) = 2Dm x (2Dm + 1)
+// (a 2Dm x 2Dm matrix with an odd leading dimension) plus small arrays.
+struct CoreSmem {
+  double* reg[5];
+  double* lam;     // [Dm]
+  double* sv;      // [2Dm]
+  int* piv;        // [4][Dm]
+  int* order;      // [2Dm]
+  int* meta;       // [16]
+  static __host__ __device__ size_t regsz(int Dm) { return 4 * (size_t)Dm * Dm + 2 * (size_t)Dm + 2; }
+  static __host__ __device__ size_t doubles(int Dm) { return 5 * regsz(Dm) + 3 * (size_t)Dm + 8; }
+  static __host__ __device__ size_t ints(int Dm) { return 6 * (size_t)Dm + 16; }
+  static __host__ __device__ size_t bytes(int Dm) { return doubles(Dm) * 8 + ints(Dm) * 4 + 16; }
+  __device__ void carve(unsigned char* base, int Dm) {
+    double* d = reinterpret_cast<double*>(base);
+    for (int i = 0; i < 5; ++i) reg[i] = d + (size_t)i * regsz(Dm);
+    lam = d + 5 * regsz(Dm);
+    sv = lam + Dm;
+    int* ip = reinterpret_cast<int*>(sv + 2 * Dm + 8);
+    piv = ip;
+    order = piv + 4 * Dm;
+    meta = order + 2 * Dm;
+  }
+};
+
+__device__ __forceinline__ Team make_team(int team_threads) {
+  Team tm;
+  tm.nt = team_threads;
+  tm.tid = threadIdx.x % team_threads;
+  tm.bar = 1 + threadIdx.x / team_threads;
+  return tm;
+}
+
+// Max |x| over the m x n column-major matrix x (ld), through a shared double slot.
+__device__ double team_absmax(const Team& tm, const double* x, int ld, int m, int n, double* slot) {
+  double v = 0.0;
+  for (int w = tm.tid; w < m * n; w += tm.nt) v = fmax(v, fabs(x[(w / m) * ld + (w % m)]));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (tm.tid == 0) *slot = 0.0;
+  tm.sync();
+  if ((tm.tid & 31) == 0) {
+    // benign max via compare-and-swap on the bit pattern (non-negative doubles order as integers)
+    unsigned long long* p = reinterpret_cast<unsigned long long*>(slot);
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+  }
+  tm.sync();
+  const double r = *slot;
+  tm.sync();
+  return r;
+}
+
+// C (m x n) = A (m x k) B (k x n), all row-major with the given leading dimensions.
+template <typename R>
+__device__ __forceinline__ void team_gemm(const Team& tm, const R* A, int lda, const R* B, int ldb, R* C, int ldc,
+                                          int m, int n, int k) {
+  for (int w = tm.tid; w < m * n; w += tm.nt) {
+    const int i = w / n, j = w % n;
+    R s = R(0);
+    for (int l = 0; l < k; ++l) s += A[i * lda + l] * B[l * ldb + j];
+    C[i * ldc + j] = s;
+  }
+}
+
+// SVD of theta (m x n, column-major, lda) preconditioned by an FP32 solve (see the file
+// comment); V column-major (ldv).  F: scratch of >= 2n(2n+1) doubles (also holds the two
+// FP32 matrices), Tt: >= n*n doubles.
+__device__ void svd_precond(const Team& tm, double* A, int lda, int m, int n, double* V, int ldv, double* F,
+                            double* Tt, int* flag, double* slot) {
+  const double amax = team_absmax(tm, A, lda, m, n, slot);
+  if (!(amax > 0.0) || n < 2) {
+    team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, true);
+    return;
+  }
+  const int la32 = odd_ld(m), lv32 = odd_ld(n);
+  float* A32 = reinterpret_cast<float*>(F);
+  float* V32 = A32 + la32 * n;
+  const double sc = 1.0 / amax;
+  for (int w = tm.tid; w < m * n; w += tm.nt) {
+    const int c = w / m, r = w % m;
+    A32[c * la32 + r] = float(A[c * lda + r] * sc);
+  }
+  tm.sync();
+  team_svd_onesided<float>(tm, A32, la32, m, n, V32, lv32, flag, 30, true);
+  for (int w = tm.tid; w < n * n; w += tm.nt) {
+    const int c = w / n, r = w % n;
+    V[c * ldv + r] = double(V32[c * lv32 + r]);
+  }
+  tm.sync();
+  // Newton-Schulz: V <- V (3I - V^T V) / 2   (Tt, F: column-major, ld n)
+  for (int w = tm.tid; w < n * n; w += tm.nt) {
+    const int j = w / n, i = w % n;
+    const double* vi = V + i * ldv;
+    const double* vj = V + j * ldv;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += vi[l] * vj[l];
+    Tt[j * n + i] = (i == j ? 1.5 : 0.0) - 0.5 * s;
+  }
+  tm.sync();
+  for (int w = tm.tid; w < n * n; w += tm.nt) {
+    const int j = w / n, i = w % n;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += V[l * ldv + i] * Tt[j * n + l];
+    F[j * n + i] = s;
+  }
+  tm.sync();
+  for (int w = tm.tid; w < n * n; w += tm.nt) V[(w / n) * ldv + (w % n)] = F[w];
+  tm.sync();
+  // A <- A V   (F: column-major, ld m)
+  for (int w = tm.tid; w < m * n; w += tm.nt) {
+    const int j = w / m, i = w % m;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += A[l * lda + i] * V[j * ldv + l];
+    F[j * m + i] = s;
+  }
+  tm.sync();
+  for (int w = tm.tid; w < m * n; w += tm.nt) A[(w / m) * lda + (w % m)] = F[w];
+  team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, false);
+}
+
+// Refinement step 1 (FP32 storage): shifted Cholesky of the four first-pass Gram blocks.
+// t1buf block layout: [T1 = R1^-1 (D x D)][R1 (D x D)] at stride chi*chi.
+template <typename R>
+__global__ void k_pre2(SweepArgs a, const GateDesc* __restrict__ gates, const R* __restrict__ gram,
+                       double* __restrict__ t1buf, int n_items, int team_threads, int Dm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Team tm = make_team(team_threads);
+  const int team = threadIdx.x / team_threads;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x / team_threads) + team;
+  if (item >= n_items) return;
+  CoreSmem sm;
+  sm.carve(smem_raw + (size_t)team * CoreSmem::bytes(Dm), Dm);
+  const int gi = (int)(item / a.B), b = (int)(item % a.B);
+  const int D = gates[gi].D, chi = a.chi, DD = D * D;
+  const R* gsrc = gram + item * 4 * chi * chi;
+  double* G = sm.reg[0];
+  double* Rf = sm.reg[1];
+  double* Ri = sm.reg[2];
+  for (int w = tm.tid; w < 4 * DD; w += tm.nt) G[w] = double(gsrc[(int64_t)(w / DD) * chi * chi + w % DD]);
+  tm.sync();
+  double ref[2];
+  for (int side = 0; side < 2; ++side) {
+    double e = 0.0;
+    for (int blk = 2 * side; blk < 2 * side + 2; ++blk)
+      for (int j = 0; j < D; ++j) e = fmax(e, G[blk * DD + j * D + j]);
+    ref[side] = e;
+  }
+  double* out = t1buf + item * 4 * 2 * chi * chi;
+  for (int blk = 0; blk < 4; ++blk) {
+    const double rf = ref[blk / 2];
+    double* T1 = out + (int64_t)blk * 2 * chi * chi;
+    double* R1 = T1 + chi * chi;
+    int r = 0;
+    if (rf > 0.0) {
+      const double shift = kPreFloor * rf;
+      for (int j = tm.tid; j < D; j += tm.nt) G[blk * DD + j * D + j] += shift;
+      tm.sync();
+      r = team_pchol<double>(tm, G + blk * DD, D, D, 0.5 * shift, Rf + blk * DD, D, sm.piv + blk * Dm, sm.meta);
+    }
+    if (r == D) {
+      team_pchol_rinv<double>(tm, Rf + blk * DD, D, sm.piv + blk * Dm, D, D, Ri + blk * DD, D);
+      for (int w = tm.tid; w < DD; w += tm.nt) {
+        T1[w] = Ri[blk * DD + w];
+        R1[w] = Rf[blk * DD + w];
+      }
+    } else {
+      // zero side (or a rounding breakdown): a plain scaling keeps T1 invertible
+      const double s = rf > 0.0 ? sqrt(rf) : 1.0;
+      for (int w = tm.tid; w < DD; w += tm.nt) {
+        const bool dg = (w / D) == (w % D);
+        T1[w] = dg ? 1.0 / s : 0.0;
+        R1[w] = dg ? s : 0.0;
+      }
+    }
+    tm.sync();
+  }
+}
+
+template <typename R>
+__global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R* __restrict__ gram,
+                        double* __restrict__ tbuf, int S, const double* __restrict__ t1buf, int n_items,
+                        int team_threads, int Dm, int precond) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Team tm = make_team(team_threads);
+  const int team = threadIdx.x / team_threads;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x / team_threads) + team;
+  if (item >= n_items) return;
+  CoreSmem sm;
+  sm.carve(smem_raw + (size_t)team * CoreSmem::bytes(Dm), Dm);
+  const int gi = (int)(item / a.B), b = (int)(item % a.B);
+  const GateDesc& gd = gates[gi];
+  const int D = gd.D, Dn = gd.Dn, chi = a.chi, DD = D * D;
+  int* meta = sm.meta;
+  double* slot = reinterpret_cast<double*>(sm.sv + 2 * Dm);   // one spare double after sv
+  const R* gsrc = gram + item * 4 * chi * chi;
+  double* RG = sm.reg[0];
+  double* RF = sm.reg[1];
+  double* RI = sm.reg[2];
+  double* TH = sm.reg[3];
+  double* VV = sm.reg[4];
+  for (int w = tm.tid; w < 4 * DD; w += tm.nt) RG[w] = double(gsrc[(int64_t)(w / DD) * chi * chi + w % DD]);
+  double* lamg = a.lam + ((int64_t)b * a.nbonds + gd.bond) * chi;
+  for (int w = tm.tid; w < D; w += tm.nt) sm.lam[w] = lamg[w];
+  tm.sync();
+  double tolv[2];
+  for (int side = 0; side < 2; ++side) {
+    double e = 0.0;
+    for (int blk = 2 * side; blk < 2 * side + 2; ++blk)
+      for (int j = 0; j < D; ++j) e = fmax(e, RG[blk * DD + j * D + j]);
+    tolv[side] = e;
+  }
+  int rk[4];
+  for (int blk = 0; blk < 4; ++blk) {
+    const double e = tolv[blk / 2];
+    rk[blk] = 0;
+    if (e > 0.0)
+      rk[blk] = team_pchol<double>(tm, RG + blk * DD, D, D, a.gram_cutoff * e, RF + blk * DD, D,
+                                   sm.piv + blk * Dm, meta);
+    if (rk[blk] > 0) team_pchol_rinv<double>(tm, RF + blk * DD, D, sm.piv + blk * Dm, rk[blk], D, RI + blk * DD, D);
+  }
+  tm.sync();
+  const double* Rm = RF;     // R factor rows (r x D, ld D) per block
+  const double* Rinv = RI;   // right inverse (D x r, ld D) per block
+  double* FF = RG;           // scratch free during the SVD
+  double* TT = RF;
+  if (t1buf) {
+    // R = R2 R1 (R1 = T1^-1) into RG, R^+ = T1 R2^+ into RF
+    const double* t1 = t1buf + item * 4 * 2 * chi * chi;
+    for (int w = tm.tid; w < 4 * DD; w += tm.nt) {
+      const int blk = w / DD, e = w % DD;
+      TH[w] = t1[(int64_t)blk * 2 * chi * chi + chi * chi + e];   // R1
+      VV[w] = t1[(int64_t)blk * 2 * chi * chi + e];               // T1
+    }
+    tm.sync();
+    for (int blk = 0; blk < 4; ++blk) {
+      const int r = rk[blk];
+      if (r == 0) continue;
+      team_gemm<double>(tm, RF + blk * DD, D, TH + blk * DD, D, RG + blk * DD, D, r, D, D);
+    }
+    tm.sync();
+    for (int blk = 0; blk < 4; ++blk) {
+      const int r = rk[blk];
+      if (r == 0) continue;
+      team_gemm<double>(tm, VV + blk * DD, D, RI + blk * DD, D, RF + blk * DD, D, D, r, D);
+    }
+    tm.sync();
+    Rm = RG;
+    Rinv = RF;
+    FF = RI;
+    TT = RG;
+  }
+  const int rAp = rk[0], rA = rk[0] + rk[1], rBp = rk[2], rB = rk[2] + rk[3];
+  double* tout = tbuf + item * 4 * chi * chi;
+  if (rA == 0 || rB == 0) {            // zero state: this shot has probability 0
+    for (int w = tm.tid; w < 4 * chi * chi; w += tm.nt) tout[w] = 0.0;
+    for (int w = tm.tid; w < Dn; w += tm.nt) lamg[w] = 0.0;
+    if (tm.tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] = -INFINITY;
+    return;
+  }
+  const double p = gd.p;
+  const double cpp = 0.5, cpm = 0.5 * (1.0 - 2.0 * p);
+  // theta[i][j] = c(ki, kj) sum_q R_{A ki}[li][q] lambda_q R_{B kj}[lj][q]  (column-major)
+  const int ldt = odd_ld(rA), ldv = odd_ld(rB);
+  for (int w = tm.tid; w < rA * rB; w += tm.nt) {
+    const int j = w / rA, i = w % rA;
+    const int ka = i < rAp ? 0 : 1, li = i - ka * rAp;
+    const int kb = j < rBp ? 0 : 1, lj = j - kb * rBp;
+    const double* ra = Rm + ka * DD + li * D;
+    const double* rb = Rm + (2 + kb) * DD + lj * D;
+    double s = 0.0;
+    for (int q = 0; q < D; ++q) s += ra[q] * sm.lam[q] * rb[q];
+    TH[j * ldt + i] = (ka == kb ? cpp : cpm) * s;
+  }
+  tm.sync();
+  if (precond)
+    svd_precond(tm, TH, ldt, rA, rB, VV, ldv, FF, TT, meta + 8, slot);
+  else
+    team_svd_onesided<double>(tm, TH, ldt, rA, rB, VV, ldv, meta + 8, 40, true);
+  team_col_norms<double>(tm, TH, ldt, rA, rB, sm.sv);
+  team_sort_desc<double>(tm, sm.sv, rB, sm.order);
+  if (tm.tid == 0) {
+    double srt[2 * kMaxChi];
+    for (int j = 0; j < rB; ++j) srt[j] = sm.sv[sm.order[j]];
+    int k = 0;
+    if (srt[0] > 0.0) k = team_keep_count<double>(srt, rB < rA ? rB : rA, Dn, a.svd_cutoff, a.multiplet_rtol);
+    meta[0] = k;
+  }
+  tm.sync();
+  const int k = meta[0];
+  const double s0 = sm.sv[sm.order[0]];
+  if (k == 0 || !(s0 > 0.0)) {
+    for (int w = tm.tid; w < 4 * chi * chi; w += tm.nt) tout[w] = 0.0;
+    for (int w = tm.tid; w < Dn; w += tm.nt) lamg[w] = 0.0;
+    if (tm.tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] = -INFINITY;
+    return;
+  }
+  const double rs2 = 0.70710678118654752440;
+  // T_{A kap}[q][j] = sum_{li} R^+_{A kap}[q][li] U[kap rows li][order j] / sqrt2, U = theta_out / s
+  for (int w = tm.tid; w < 2 * D * Dn; w += tm.nt) {
+    const int kap = w / (D * Dn), q = (w / Dn) % D, j = w % Dn;
+    double acc = 0.0;
+    if (j < k) {
+      const int cj = sm.order[j];
+      const int r = rk[kap], off = kap ? rAp : 0;
+      const double* ri = Rinv + kap * DD + q * D;
+      const double* u = TH + cj * ldt + off;
+      for (int li = 0; li < r; ++li) acc += ri[li] * u[li];
+      acc /= sm.sv[cj];
+    }
+    tout[(int64_t)kap * chi * chi + q * Dn + j] = acc * rs2;
+  }
+  for (int w = tm.tid; w < 2 * D * Dn; w += tm.nt) {
+    const int kap = w / (D * Dn), q = (w / Dn) % D, j = w % Dn;
+    double acc = 0.0;
+    if (j < k) {
+      const int cj = sm.order[j];
+      const int r = rk[2 + kap], off = kap ? rBp : 0;
+      const double* ri = Rinv + (2 + kap) * DD + q * D;
+      const double* v = VV + cj * ldv + off;
+      for (int lj = 0; lj < r; ++lj) acc += ri[lj] * v[lj];
+    }
+    tout[(int64_t)(2 + kap) * chi * chi + q * Dn + j] = acc * rs2;
+  }
+  for (int j = tm.tid; j < Dn; j += tm.nt) lamg[j] = (j < k) ? sm.sv[sm.order[j]] / s0 : 0.0;
+  if (tm.tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] += log(s0);
+}
+
+// ---- launch configuration ---------------------------------------------------------------
+// Team size by bond dimension: small cores get one warp each (8 per block), larger ones a
+// group of warps, so that no block-wide barrier serialises independent gates.
+static void core_shape(int Dm, int& team_threads, int& teams) {
+  if (Dm <= 8) { team_threads = 32; teams = 8; }
+  else if (Dm <= 16) { team_threads = 64; teams = 2; }
+  else { team_threads = 128; teams = 1; }
+}
+
+size_t core2_smem_bytes(int Dm) {
+  int tt, teams;
+  core_shape(Dm, tt, teams);
+  return (size_t)teams * CoreSmem::bytes(Dm);
+}
+
+template <typename R>
+cudaError_t launch_core2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* tbuf,
+                         const double* t1buf, int S, bool precond, cudaStream_t st) {
+  int tt, teams;
+  core_shape(Dm, tt, teams);
+  const int64_t n_items = (int64_t)count * a.B;
+  const size_t smem = (size_t)teams * CoreSmem::bytes(Dm);
+  cudaError_t e = cudaFuncSetAttribute(k_core2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((n_items + teams - 1) / teams);
+  k_core2<R><<<blocks, tt * teams, smem, st>>>(a, g, reinterpret_cast<const R*>(gram), tbuf, S, t1buf,
+                                                (int)n_items, tt, Dm, precond ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pre2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* t1buf,
+                        cudaStream_t st) {
+  int tt, teams;
+  core_shape(Dm, tt, teams);
+  const int64_t n_items = (int64_t)count * a.B;
+  const size_t smem = (size_t)teams * CoreSmem::bytes(Dm);
+  cudaError_t e = cudaFuncSetAttribute(k_pre2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((n_items + teams - 1) / teams);
+  k_pre2<R><<<blocks, tt * teams, smem, st>>>(a, g, reinterpret_cast<const R*>(gram), t1buf, (int)n_items, tt, Dm);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_core2<double>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
+                                          const double*, int, bool, cudaStream_t);
+template cudaError_t launch_core2<float>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
+                                         const double*, int, bool, cudaStream_t);
+template cudaError_t launch_pre2<float>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
+                                        cudaStream_t);
+template cudaError_t launch_pre2<double>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
+                                         cudaStream_t);
+
+}  // namespace td

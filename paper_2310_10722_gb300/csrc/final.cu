@@ -11,111 +11,114 @@
 #include <cmath>
 #include <mutex>
 
-#include "linalg.cuh"
 #include "sweep.cuh"
+#include "team.cuh"
 
 namespace td {
 
+// F[c][l][r][d][u] of site (x, y) into F (dims into fd: L, R, D, U).  sqrt(lambda) of the
+// site's bonds is staged in slam[4][chi] first.
 template <typename R>
-__device__ void build_F(const FinalArgs& fa, int b, int x, int y, R* F, int* fd) {
-  // fd: dims (L, R, D, U) of the site
+__device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y, R* F, int* fd, R* slam) {
   const int s = fa.grid_site[y * fa.nx + x];
   if (s < 0) {
-    if (threadIdx.x == 0) { F[0] = R(1); F[1] = R(0); }
-    if (threadIdx.x < 4) fd[threadIdx.x] = 1;
-    __syncthreads();
+    if (tm.tid == 0) { F[0] = R(1); F[1] = R(0); }
+    if (tm.tid < 4) fd[tm.tid] = 1;
+    tm.sync();
     return;
   }
   const FinalSite& fs = fa.sites[s];
+  const double* lam = fa.lam + (int64_t)b * fa.nbonds * fa.chi;
+  for (int w = tm.tid; w < 4 * fa.chi; w += tm.nt) {
+    const int dir = w / fa.chi, i = w % fa.chi;
+    slam[w] = (fs.dir_pos[dir] >= 0 && i < fs.dir_dim[dir]) ? R(sqrt(lam[fs.dir_bond[dir] * fa.chi + i])) : R(1);
+  }
   const int dL = fs.dir_dim[0], dR = fs.dir_dim[1], dD = fs.dir_dim[2], dU = fs.dir_dim[3];
-  int stride[kMaxBonds];
+  int stride[4];   // stride of each direction's index in the site tensor (0 if absent)
   {
-    int st = 1;
+    int st[kMaxBonds];
+    int acc = 1;
     for (int k = fs.nb - 1; k >= 0; --k) {
-      stride[k] = st;
+      st[k] = acc;
       int dk = 1;
       for (int dir = 0; dir < 4; ++dir)
         if (fs.dir_pos[dir] == k) dk = fs.dir_dim[dir];
-      st *= dk;
+      acc *= dk;
     }
+    for (int dir = 0; dir < 4; ++dir) stride[dir] = fs.dir_pos[dir] >= 0 ? st[fs.dir_pos[dir]] : 0;
   }
-  int rest = 1;
-  for (int dir = 0; dir < 4; ++dir) rest *= fs.dir_dim[dir];
-  const int64_t shot = (int64_t)b * fa.shot_elems;
-  const double* lam = fa.lam + (int64_t)b * fa.nbonds * fa.chi;
-  const int n = dL * dR * dD * dU;
-  for (int w = threadIdx.x; w < 2 * n; w += blockDim.x) {
-    const int c = w / n;
-    int e = w % n;
+  const int rest = dL * dR * dD * dU;
+  const R* g = reinterpret_cast<const R*>(fa.gamma) + (int64_t)b * fa.shot_elems + fs.off;
+  tm.sync();
+  for (int w = tm.tid; w < rest; w += tm.nt) {
+    int e = w;
     const int iu = e % dU; e /= dU;
     const int id = e % dD; e /= dD;
     const int ir = e % dR; e /= dR;
     const int il = e;
-    const int idx[4] = {il, ir, id, iu};
-    int64_t off = 0;
-    R wgt = R(1);
-    for (int dir = 0; dir < 4; ++dir)
-      if (fs.dir_pos[dir] >= 0) {
-        off += (int64_t)idx[dir] * stride[fs.dir_pos[dir]];
-        wgt *= R(sqrt(lam[fs.dir_bond[dir] * fa.chi + idx[dir]]));
-      }
-    R acc = R(0);
+    const int off = il * stride[0] + ir * stride[1] + id * stride[2] + iu * stride[3];
+    const R wgt = slam[il] * slam[fa.chi + ir] * slam[2 * fa.chi + id] * slam[3 * fa.chi + iu];
+    R a0 = R(0), a1 = R(0);
     for (int ph = 0; ph < fs.P; ++ph) {
-      const double rr = fs.R[ph * 2 + c];
-      if (rr == 0.0) continue;
-      R g = reinterpret_cast<const R*>(fa.gamma)[shot + fs.off + (int64_t)ph * rest + off];
-      acc += R(rr) * g;
+      const R gv = g[(int64_t)ph * rest + off];
+      a0 += R(fs.R[ph * 2 + 0]) * gv;
+      a1 += R(fs.R[ph * 2 + 1]) * gv;
     }
-    F[w] = acc * wgt;
+    F[w] = a0 * wgt;
+    F[rest + w] = a1 * wgt;
   }
-  if (threadIdx.x == 0) { fd[0] = dL; fd[1] = dR; fd[2] = dD; fd[3] = dU; }
-  __syncthreads();
+  if (tm.tid == 0) { fd[0] = dL; fd[1] = dR; fd[2] = dD; fd[3] = dU; }
+  tm.sync();
 }
 
+// One block per shot.  The work region (site tensor F, T1 / V, M^T, carries) lives in
+// shared memory when it fits, otherwise in the shot's global scratch; the boundary MPS is
+// always in global scratch.
 template <typename R>
 __global__ void k_final(FinalArgs fa) {
   const int b = blockIdx.x;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const Team tm{(int)threadIdx.x, (int)blockDim.x, 1};
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   R* scr = reinterpret_cast<R*>(fa.scratch) + (int64_t)b * fa.scratch_elems;
+  R* work = fa.use_smem ? reinterpret_cast<R*>(smem_raw) : scr + fa.off_work;
   R* mps[2] = {scr + fa.off_mps0, scr + fa.off_mps1};
-  R* Cb[2] = {scr + fa.off_C0, scr + fa.off_C1};
-  R* F = scr + fa.off_F;
-  R* T1 = scr + fa.off_T1;
-  R* Tm = scr + fa.off_T;
-  R* G = scr + fa.off_G;
-  R* V = scr + fa.off_V;
-  R* sv = scr + fa.off_s;
+  R* F = work + fa.w_F;
+  R* W = work + fa.w_W;        // T1, then V of the SVD
+  R* MT = work + fa.w_MT;      // M^T (n x m)
+  R* Cb[2] = {work + fa.w_C0, work + fa.w_C1};
+  R* sv = work + fa.w_s;
+  int* ord = reinterpret_cast<int*>(work + fa.w_ord);
   __shared__ int mdim[2][32][3];   // per column: (left, down, right) of the MPS tensors
   __shared__ int fd[4];
   __shared__ int meta[8];
-  __shared__ R rot[2 * 160];
-  __shared__ int order_s[1];
+  __shared__ R slam[4 * kMaxChi];
   __shared__ double logsum_s;
   const int nx = fa.nx, ny = fa.ny;
-  if (tid == 0) logsum_s = 0.0;
-  for (int x = tid; x < nx; x += nt) {
+  if (tm.tid == 0) logsum_s = 0.0;
+  for (int x = tm.tid; x < nx; x += tm.nt) {
     mdim[0][x][0] = 1; mdim[0][x][1] = 1; mdim[0][x][2] = (x == nx - 1) ? 2 : 1;
     R* A = mps[0] + (int64_t)x * fa.mps_stride;
     A[0] = R(1);
     if (x == nx - 1) A[1] = R(0);
   }
-  __syncthreads();
+  tm.sync();
   int cur = 0;
   for (int y = 0; y < ny; ++y) {
     int cc = 0;
-    // carry C[j][a][l][p]: j = 1, a = 1, l = 1, p = 0
-    if (tid == 0) { Cb[0][0] = R(1); Cb[0][1] = R(0); }
+    if (tm.tid == 0) { Cb[0][0] = R(1); Cb[0][1] = R(0); }
     int cJ = 1, cA = 1, cL = 1;
-    __syncthreads();
+    tm.sync();
     for (int x = 0; x < nx; ++x) {
-      build_F<R>(fa, b, x, y, F, fd);
-      const int L = fd[0], Rr = fd[1], Dd = fd[2], U = fd[3];
+      build_F<R>(tm, fa, b, x, y, F, fd, slam);
+      const int L = fd[0], Rr = fd[1], U = fd[3];
       const R* A = mps[cur] + (int64_t)x * fa.mps_stride;
       const int aL = mdim[cur][x][0], aD = mdim[cur][x][1], aR = mdim[cur][x][2];
       const R* C = Cb[cc];
-      // T1[j][l][p][d][bb] = sum_a C[j][a][l][p] A[a][d][bb]   (a: cA == aL, d: Dd == aD, l: cL == L)
+      (void)cA;
+      // T1[j][l][p][d][bb] = sum_a C[j][a][l][p] A[a][d][bb]
+      R* T1 = W;
       const int n1 = cJ * L * 2 * aD * aR;
-      for (int w = tid; w < n1; w += nt) {
+      for (int w = tm.tid; w < n1; w += tm.nt) {
         int e = w;
         const int bb = e % aR; e /= aR;
         const int d = e % aD; e /= aD;
@@ -123,83 +126,68 @@ __global__ void k_final(FinalArgs fa) {
         const int l = e % L; e /= L;
         const int j = e;
         R acc = R(0);
-        for (int a = 0; a < aL; ++a) acc += C[((j * cA + a) * cL + l) * 2 + p] * A[(a * aD + d) * aR + bb];
+        for (int a = 0; a < aL; ++a) acc += C[((j * aL + a) * cL + l) * 2 + p] * A[(a * aD + d) * aR + bb];
         T1[w] = acc;
       }
-      __syncthreads();
-      // Tm[j][u][bb][r][q] = sum_{l,p,d} T1[j][l][p][d][bb] F[p^q][l][r][d][u]
-      const int nF = L * Rr * Dd * U;
-      const int n2 = cJ * U * aR * Rr * 2;
-      for (int w = tid; w < n2; w += nt) {
-        int e = w;
-        const int q = e % 2; e /= 2;
-        const int r = e % Rr; e /= Rr;
-        const int bb = e % aR; e /= aR;
-        const int u = e % U; e /= U;
-        const int j = e;
+      tm.sync();
+      // MT[(bb, r, q)][(j, u)] = sum_{l,p,d} T1[j][l][p][d][bb] F[p^q][l][r][d][u], stored
+      // column-major: column (j, u) of MT is row (j, u) of M (ld ldm, odd)
+      const int nF = L * Rr * aD * U;
+      const int m = cJ * U, n = aR * Rr * 2;
+      const int ldm = odd_ld(n), ldv = odd_ld(m);
+      for (int w = tm.tid; w < m * n; w += tm.nt) {
+        const int ju = w / n, c = w % n;
+        const int q = c % 2, r = (c / 2) % Rr, bb = c / (2 * Rr);
+        const int j = ju / U, u = ju % U;
         R acc = R(0);
         for (int l = 0; l < L; ++l)
-          for (int p = 0; p < 2; ++p)
-            for (int d = 0; d < aD; ++d)
-              acc += T1[(((j * L + l) * 2 + p) * aD + d) * aR + bb] * F[(p ^ q) * nF + ((l * Rr + r) * Dd + d) * U + u];
-        Tm[w] = acc;
-      }
-      __syncthreads();
-      R* An = mps[cur ^ 1] + (int64_t)x * fa.mps_stride;
-      const int m = cJ * U, n = aR * Rr * 2;
-      if (x < nx - 1 && y < ny - 1) {
-        // SVD of M = Tm [(j,u) x (b,r,q)] by one-sided Jacobi on the rows of M: the columns
-        // of MT = M^T are orthogonalised, MT W = (S V^T)^T, W = left singular vectors.
-        R* MT = G;
-        for (int w = tid; w < m * n; w += nt) {
-          const int ju = w / n, c = w % n;
-          MT[c * m + ju] = Tm[w];
-        }
-        __syncthreads();
-        block_svd_onesided<R>(MT, m, n, m, V, m, rot, meta + 7);
-        int* ord = reinterpret_cast<int*>(Tm + m * n);   // scratch after Tm (sized on host)
-        for (int j = tid; j < m; j += nt) {
-          R s2 = R(0);
-          for (int c = 0; c < n; ++c) s2 += MT[c * m + j] * MT[c * m + j];
-          sv[m + j] = sqrt(s2);
-        }
-        __syncthreads();
-        if (tid == 0) {
-          for (int i = 0; i < m; ++i) ord[i] = i;
-          for (int i = 1; i < m; ++i) {
-            int xk = ord[i], k = i - 1;
-            while (k >= 0 && sv[m + ord[k]] < sv[m + xk]) { ord[k + 1] = ord[k]; --k; }
-            ord[k + 1] = xk;
+          for (int p = 0; p < 2; ++p) {
+            const R* t1 = T1 + (((j * L + l) * 2 + p) * aD) * aR + bb;
+            const R* f = F + (p ^ q) * nF + ((l * Rr + r) * aD) * U + u;
+            for (int d = 0; d < aD; ++d) acc += t1[d * aR] * f[d * U];
           }
-          for (int i = 0; i < m; ++i) sv[i] = sv[m + ord[i]];
+        MT[ju * ldm + c] = acc;
+      }
+      tm.sync();
+      R* An = mps[cur ^ 1] + (int64_t)x * fa.mps_stride;
+      R* Cn = Cb[cc ^ 1];
+      if (x < nx - 1 && y < ny - 1) {
+        // left singular vectors of M = MT^T: one-sided Jacobi on the m columns of MT
+        R* V = W;
+        team_svd_onesided<R>(tm, MT, ldm, n, m, V, ldv, meta + 7, 40, true);
+        team_col_norms<R>(tm, MT, ldm, n, m, sv);
+        team_sort_desc<R>(tm, sv, m, ord);
+        if (tm.tid == 0) {
           int k = 0;
-          const int nsv = m < n ? m : n;
-          if (sv[0] > R(0)) k = keep_count<R>(sv, nsv, fa.chi_mps, fa.svd_cutoff, fa.multiplet_rtol);
+          const R s0 = sv[ord[0]];
+          if (s0 > R(0)) {
+            R srt[2 * 256 / 2];
+            const int nsv = m < n ? m : n;
+            for (int i = 0; i < nsv; ++i) srt[i] = sv[ord[i]];
+            k = team_keep_count<R>(srt, nsv, fa.chi_mps, fa.svd_cutoff, fa.multiplet_rtol);
+          }
           meta[0] = k;
         }
-        __syncthreads();
+        tm.sync();
         const int k = meta[0];
         if (k == 0) {
-          if (tid == 0) logsum_s = -INFINITY;
-          // keep a single zero column so shapes stay valid
-          for (int w = tid; w < m; w += nt) An[w] = R(0);
-          R* Cn = Cb[cc ^ 1];
-          for (int w = tid; w < n; w += nt) Cn[w] = R(0);
-          __syncthreads();
-          if (tid == 0) { mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = 1; }
+          if (tm.tid == 0) logsum_s = -INFINITY;
+          for (int w = tm.tid; w < m; w += tm.nt) An[w] = R(0);
+          for (int w = tm.tid; w < n; w += tm.nt) Cn[w] = R(0);
+          if (tm.tid == 0) { mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = 1; }
           cJ = 1;
         } else {
-          const R s0 = sv[0];
-          for (int w = tid; w < m * k; w += nt) {
+          const R s0 = sv[ord[0]];
+          const R inv0 = R(1) / s0;
+          for (int w = tm.tid; w < m * k; w += tm.nt) {
             const int ju = w / k, kk = w % k;
-            An[w] = V[ju * m + ord[kk]];            // An[j][u][kk]
+            An[w] = V[ord[kk] * ldv + ju];
           }
-          R* Cn = Cb[cc ^ 1];
-          for (int w = tid; w < k * n; w += nt) {
+          for (int w = tm.tid; w < k * n; w += tm.nt) {
             const int kk = w / n, c = w % n;
-            Cn[w] = MT[c * m + ord[kk]] / s0;       // Cn[kk][bb][r][q] = (S V^T)[kk][c] / s0
+            Cn[w] = MT[ord[kk] * ldm + c] * inv0;
           }
-          if (tid == 0) {
+          if (tm.tid == 0) {
             logsum_s += log((double)s0);
             mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = k;
           }
@@ -207,57 +195,64 @@ __global__ void k_final(FinalArgs fa) {
         }
         cA = aR; cL = Rr;
         cc ^= 1;
-        __syncthreads();
+        tm.sync();
       } else if (x < nx - 1) {
         // last row: U == 1, no truncation; the carry takes the whole contraction
-        R* Cn = Cb[cc ^ 1];
-        for (int w = tid; w < m * n; w += nt) Cn[w] = Tm[w];
-        for (int w = tid; w < m * m; w += nt) An[w] = (w / m == w % m) ? R(1) : R(0);
-        if (tid == 0) { mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = m; }
+        for (int w = tm.tid; w < m * n; w += tm.nt) {
+          const int ju = w / n, c = w % n;
+          Cn[w] = MT[ju * ldm + c];
+        }
+        for (int w = tm.tid; w < m * m; w += tm.nt) An[w] = (w / m == w % m) ? R(1) : R(0);
+        if (tm.tid == 0) { mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = m; }
         cJ = m; cA = aR; cL = Rr;
         cc ^= 1;
-        __syncthreads();
+        tm.sync();
       } else {
-        // last column: merge the old class leg bb and the row parity q into c' = bb ^ q
-        if (tid == 0) {
-          R mx = R(0);
-          for (int ju = 0; ju < m; ++ju)
-            for (int c2 = 0; c2 < 2; ++c2) {
-              R acc = R(0);
-              for (int bb = 0; bb < aR; ++bb)
-                for (int q = 0; q < 2; ++q)
-                  if ((bb ^ q) == c2) acc += Tm[((ju * aR + bb) * Rr + 0) * 2 + q];
-              An[ju * 2 + c2] = acc;
-              mx = fmax(mx, fabs(acc));
-            }
-          if (mx > R(0)) {
-            for (int w = 0; w < m * 2; ++w) An[w] /= mx;
-            logsum_s += log((double)mx);
-          } else {
-            logsum_s = -INFINITY;
-          }
-          mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = 2;
+        // last column (Rr == 1): merge the old class leg bb and the row parity q into bb ^ q
+        for (int w = tm.tid; w < m * 2; w += tm.nt) {
+          const int ju = w / 2, c2 = w % 2;
+          R acc = R(0);
+          for (int bb = 0; bb < aR; ++bb) acc += MT[ju * ldm + bb * 2 + (bb ^ c2)];
+          An[w] = acc;
         }
-        __syncthreads();
+        tm.sync();
+        if (tm.tid < 32) {
+          R mx = R(0);
+          for (int w = tm.tid; w < m * 2; w += 32) mx = fmax(mx, fabs(An[w]));
+          for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          if (tm.tid == 0) {
+            meta[1] = 0;
+            if (mx > R(0)) logsum_s += log((double)mx); else logsum_s = -INFINITY;
+            slam[0] = mx;
+            mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = 2;
+          }
+        }
+        tm.sync();
+        const R mx = slam[0];
+        if (mx > R(0)) {
+          const R inv = R(1) / mx;
+          for (int w = tm.tid; w < m * 2; w += tm.nt) An[w] *= inv;
+        }
+        tm.sync();
       }
     }
     cur ^= 1;
-    __syncthreads();
+    tm.sync();
   }
-  if (tid == 0) {
+  if (tm.tid == 0) {
     // contract the last MPS (vertical legs are trivial): v <- v A_x
-    R v[64], vn[64];
+    R v[256], vn[256];
     v[0] = R(1);
     int dv = 1;
     for (int x = 0; x < nx; ++x) {
       const R* A = mps[cur] + (int64_t)x * fa.mps_stride;
       const int aL = mdim[cur][x][0], aR = mdim[cur][x][2];
-      for (int bb = 0; bb < aR && bb < 64; ++bb) {
+      for (int bb = 0; bb < aR && bb < 256; ++bb) {
         R acc = R(0);
         for (int a = 0; a < aL && a < dv; ++a) acc += v[a] * A[a * aR + bb];
         vn[bb] = acc;
       }
-      dv = aR < 64 ? aR : 64;
+      dv = aR < 256 ? aR : 256;
       for (int bb = 0; bb < dv; ++bb) v[bb] = vn[bb];
     }
     fa.Z[(int64_t)b * 2 + 0] = double(v[0]);
@@ -295,7 +290,13 @@ __global__ void k_finalize(FinalizeArgs f) {
 
 template <typename T, typename R>
 cudaError_t launch_final(const FinalArgs& f, cudaStream_t st) {
-  k_final<R><<<f.B, 256, 0, st>>>(f);
+  size_t smem = 0;
+  if (f.use_smem) {
+    smem = (size_t)f.work_elems * sizeof(R);
+    cudaError_t e = cudaFuncSetAttribute(k_final<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_final<R><<<f.B, 256, smem, st>>>(f);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,6 @@
 #include <cfloat>
 #include <cmath>
 
-#include "linalg.cuh"
 #include "sweep.cuh"
 
 namespace td {
@@ -234,211 +233,6 @@ __global__ void k_gram(SweepArgs a, const GateDesc* __restrict__ gates, R* __res
   }
 }
 
-// Refinement step 1 (FP32 storage): eigen-decompose the four first-pass Gram blocks in FP64
-// and emit T1 = W Sigma^-1 and T1^-1 = Sigma W^T per block.  Eigenvalues are floored at
-// kPreFloor of the side's largest -- the rounding level of an FP32 Gram -- so T1 stays
-// invertible, no direction is dropped here, and every column of Q1 = M T1 has norm O(1)
-// or less (a floored direction is resolved by the second Gram instead).
-constexpr double kPreFloor = 1e-6;
-template <typename R>
-__global__ void k_pre(SweepArgs a, const GateDesc* __restrict__ gates, const R* __restrict__ gram,
-                      double* __restrict__ t1buf) {
-  const int gi = blockIdx.x, b = blockIdx.y;
-  const int D = gates[gi].D, chi = a.chi;
-  extern __shared__ double sm[];
-  double* G = sm;                 // [4][D*D]
-  double* V = G + 4 * D * D;      // [4][D*D]
-  double* rot = V + 4 * D * D;    // [D + 2]
-  int* flag = reinterpret_cast<int*>(rot + D + 2);
-  const R* gsrc = gram + (int64_t)(gi * a.B + b) * 4 * chi * chi;
-  for (int w = threadIdx.x; w < 4 * D * D; w += blockDim.x)
-    G[w] = double(gsrc[(int64_t)(w / (D * D)) * chi * chi + w % (D * D)]);
-  __syncthreads();
-  for (int blk = 0; blk < 4; ++blk) block_sym_eig<double>(G + blk * D * D, D, V + blk * D * D, D, D, rot, flag);
-  __syncthreads();
-  double* out = t1buf + (int64_t)(gi * a.B + b) * 4 * 2 * chi * chi;
-  for (int w = threadIdx.x; w < 4 * D * D; w += blockDim.x) {
-    const int blk = w / (D * D), q = (w / D) % D, j = w % D;
-    const int side = blk / 2;
-    double emax = 0;
-    for (int bb = 2 * side; bb < 2 * side + 2; ++bb)
-      for (int i = 0; i < D; ++i) emax = fmax(emax, G[bb * D * D + i * D + i]);
-    double* o = out + (int64_t)blk * 2 * chi * chi;
-    if (emax <= 0) {
-      o[q * D + j] = (q == j) ? 1.0 : 0.0;
-      o[chi * chi + q * D + j] = (q == j) ? 1.0 : 0.0;
-      continue;
-    }
-    const double e = fmax(G[blk * D * D + j * D + j], kPreFloor * emax);
-    const double s = sqrt(e);
-    o[q * D + j] = V[blk * D * D + q * D + j] / s;                     // T1[q][j]
-    const double ej = fmax(G[blk * D * D + q * D + q], kPreFloor * emax);
-    o[chi * chi + q * D + j] = sqrt(ej) * V[blk * D * D + j * D + q];  // T1^-1[q][j] = s_q W[j][q]
-  }
-}
-
-// Simple-update core of one gate (FP64): eigen-decompose the four Gram blocks, build theta,
-// SVD it, truncate, emit T+- for both sides and the new lambda of the bond.
-// With t1buf the Gram blocks are those of Q1 = M T1: the R factor of a block is
-// Sigma W^T T1^-1 and the update transform T1 W Sigma^-1 U.
-template <typename R>
-__global__ void k_core(SweepArgs a, const GateDesc* __restrict__ gates, const R* __restrict__ gram,
-                       double* __restrict__ tbuf, int S, const double* __restrict__ t1buf) {
-  const int gi = blockIdx.x, b = blockIdx.y;
-  const GateDesc& gd = gates[gi];
-  const int D = gd.D, Dn = gd.Dn, chi = a.chi;
-  const int D2 = 2 * D;
-  extern __shared__ double sm[];
-  double* G = sm;                       // [4][D*D]
-  double* V = G + 4 * D * D;            // [4][D*D]
-  double* th = V + 4 * D * D;           // [D2][D2]
-  double* Vt = th + D2 * D2;            // [D2][D2]
-  double* sA = Vt + D2 * D2;            // [D2] kept sigma of A
-  double* sB = sA + D2;                 // [D2]
-  double* sv = sB + D2;                 // [D2] singular values (unsorted)
-  double* lamb = sv + D2;               // [D]
-  double* rot = lamb + D + 1;           // [D2 + 2]
-  int* iA = reinterpret_cast<int*>(rot + D2 + 2);   // [D2] kept index (block*D + j)
-  int* iB = iA + D2;
-  int* order = iB + D2;                 // [D2]
-  int* meta = order + D2;               // [8]
-  double* Wt = reinterpret_cast<double*>(meta + 8);   // [4][D*D] (refinement only)
-  double* Wf = Wt + 4 * D * D;                        // [4][D*D]
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const R* gsrc = gram + (int64_t)(gi * a.B + b) * 4 * chi * chi;
-  for (int w = tid; w < 4 * D * D; w += nt) {
-    const int blk = w / (D * D), e = w % (D * D);
-    G[w] = double(gsrc[(int64_t)blk * chi * chi + e]);
-  }
-  double* lamg = a.lam + ((int64_t)b * a.nbonds + gd.bond) * chi;
-  for (int w = tid; w < D; w += nt) lamb[w] = lamg[w];
-  __syncthreads();
-  for (int blk = 0; blk < 4; ++blk)
-    block_sym_eig<double>(G + blk * D * D, D, V + blk * D * D, D, D, rot, meta + 7);
-  __syncthreads();
-  const double* WtU = V;   // rows of R = Sigma (W^T T1^-1): WtU[q][j] = (T1^-T W)[q][j]
-  const double* WfU = V;   // columns of the update transform: WfU = T1 W
-  if (t1buf) {
-    const double* t1 = t1buf + (int64_t)(gi * a.B + b) * 4 * 2 * chi * chi;
-    for (int w = tid; w < 4 * D * D; w += nt) {
-      const int blk = w / (D * D), q = (w / D) % D, j = w % D;
-      const double* T1 = t1 + (int64_t)blk * 2 * chi * chi;
-      const double* Ti = T1 + chi * chi;
-      const double* W = V + blk * D * D;
-      double at = 0, af = 0;
-      for (int r = 0; r < D; ++r) {
-        at += Ti[r * D + q] * W[r * D + j];
-        af += T1[q * D + r] * W[r * D + j];
-      }
-      Wt[w] = at;
-      Wf[w] = af;
-    }
-    __syncthreads();
-    WtU = Wt;
-    WfU = Wf;
-  }
-  if (tid == 0) {
-    // keep Gram eigen-directions above gram_cutoff * largest eigenvalue of that side
-    for (int side = 0; side < 2; ++side) {
-      double emax = 0;
-      for (int blk = 0; blk < 2; ++blk)
-        for (int j = 0; j < D; ++j) emax = fmax(emax, G[(2 * side + blk) * D * D + j * D + j]);
-      int r = 0;
-      for (int blk = 0; blk < 2; ++blk)
-        for (int j = 0; j < D; ++j) {
-          const double e = G[(2 * side + blk) * D * D + j * D + j];
-          if (emax > 0 && e > a.gram_cutoff * emax) {
-            (side ? iB : iA)[r] = blk * D + j;
-            (side ? sB : sA)[r] = sqrt(e);
-            ++r;
-          }
-        }
-      meta[side] = r;
-    }
-  }
-  __syncthreads();
-  const int rA = meta[0], rB = meta[1];
-  const double p = gd.p;
-  const double cpp = 0.5, cpm = 0.5 * (1.0 - 2.0 * p);
-  double* tout = tbuf + (int64_t)(gi * a.B + b) * 4 * chi * chi;
-  if (rA == 0 || rB == 0) {                  // zero state: this shot has probability 0
-    for (int w = tid; w < 4 * chi * chi; w += nt) tout[w] = 0.0;
-    for (int w = tid; w < Dn; w += nt) lamg[w] = 0.0;
-    if (tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] = -INFINITY;
-    return;
-  }
-  // theta[i][j] = sA_i sB_j c(ki,kj) sum_b W_A[b][i'] lambda_b W_B[b][j']
-  for (int w = tid; w < rA * rB; w += nt) {
-    const int i = w / rB, j = w % rB;
-    const int ba = iA[i] / D, ja = iA[i] % D, bb = iB[j] / D, jb = iB[j] % D;
-    const double* WA = WtU + ba * D * D;
-    const double* WB = WtU + (2 + bb) * D * D;
-    double acc = 0;
-    for (int q = 0; q < D; ++q) acc += WA[q * D + ja] * lamb[q] * WB[q * D + jb];
-    th[i * rB + j] = sA[i] * sB[j] * (ba == bb ? cpp : cpm) * acc;
-  }
-  __syncthreads();
-  block_svd_onesided<double>(th, rB, rA, rB, Vt, rB, rot, meta + 7);
-  for (int j = tid; j < rB; j += nt) {
-    double s2 = 0;
-    for (int i = 0; i < rA; ++i) s2 += th[i * rB + j] * th[i * rB + j];
-    sv[j] = sqrt(s2);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int j = 0; j < rB; ++j) order[j] = j;
-    for (int j = 1; j < rB; ++j) {           // insertion sort, descending
-      int x = order[j], k = j - 1;
-      while (k >= 0 && sv[order[k]] < sv[x]) { order[k + 1] = order[k]; --k; }
-      order[k + 1] = x;
-    }
-    double srt[2 * kMaxChi];
-    for (int j = 0; j < rB; ++j) srt[j] = sv[order[j]];
-    int k = 0;
-    if (srt[0] > 0) k = keep_count<double>(srt, rB < rA ? rB : rA, Dn, a.svd_cutoff, a.multiplet_rtol);
-    meta[2] = k;
-  }
-  __syncthreads();
-  const int k = meta[2];
-  const double s0 = sv[order[0]];
-  if (k == 0 || !(s0 > 0)) {
-    for (int w = tid; w < 4 * chi * chi; w += nt) tout[w] = 0.0;
-    for (int w = tid; w < Dn; w += nt) lamg[w] = 0.0;
-    if (tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] = -INFINITY;
-    return;
-  }
-  const double rs2 = 0.70710678118654752440;
-  // T_A(kappa)[q][j] = sum_{i in A kappa} W_A[q][i'] / sA_i * U[i][j] / sqrt2, U[:, j] = th[:, order j] / s_j
-  for (int w = tid; w < 2 * D * Dn; w += nt) {
-    const int kap = w / (D * Dn), q = (w / Dn) % D, j = w % Dn;
-    double acc = 0;
-    if (j < k) {
-      const int cj = order[j];
-      const double inv = 1.0 / sv[cj];
-      for (int i = 0; i < rA; ++i) {
-        if (iA[i] / D != kap) continue;
-        acc += WfU[kap * D * D + q * D + (iA[i] % D)] / sA[i] * th[i * rB + cj] * inv;
-      }
-    }
-    tout[(int64_t)kap * chi * chi + q * Dn + j] = acc * rs2;
-  }
-  for (int w = tid; w < 2 * D * Dn; w += nt) {
-    const int kap = w / (D * Dn), q = (w / Dn) % D, j = w % Dn;
-    double acc = 0;
-    if (j < k) {
-      const int cj = order[j];
-      for (int i = 0; i < rB; ++i) {
-        if (iB[i] / D != kap) continue;
-        acc += WfU[(2 + kap) * D * D + q * D + (iB[i] % D)] / sB[i] * Vt[i * rB + cj];
-      }
-    }
-    tout[(int64_t)(2 + kap) * chi * chi + q * Dn + j] = acc * rs2;
-  }
-  __syncthreads();
-  for (int j = tid; j < Dn; j += nt) lamg[j] = (j < k) ? sv[order[j]] / s0 : 0.0;
-  if (tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] += log(s0);
-}
-
 constexpr int kUpdRows = 32;
 
 // Gamma_new[lo] = Y T+ + Z T-, Gamma_new[hi] = Y T+ - Z T- for a tile of rows of one side.
@@ -515,12 +309,6 @@ cudaError_t launch_local(const SweepArgs& a, const LocalDesc* locals, int S, cud
   return cudaGetLastError();
 }
 
-size_t core_smem_bytes(int D) {
-  const int D2 = 2 * D;
-  return sizeof(double) * (8 * D * D + 2 * D2 * D2 + 3 * D2 + D + 1 + D2 + 2) + sizeof(int) * (4 * D2 + 8) +
-         sizeof(double) * 8 * D * D + 64;
-}
-
 template <typename T, typename R>
 cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round& rd, void* gram, double* tbuf,
                          double* t1buf, int S, cudaStream_t st, Prof* prof) {
@@ -537,15 +325,9 @@ cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round&
   if (e != cudaSuccess) return e;
   const bool refine = t1buf != nullptr;
   if (refine) {
-    const size_t smem_p = sizeof(double) * (8 * D * D + D + 2) + 16;
-    if (smem_p > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_pre<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p);
-      if (e != cudaSuccess) return e;
-    }
     B(TD_K_PRE);
-    k_pre<R><<<dim3(rd.count, a.B), 128, smem_p, st>>>(a, g, reinterpret_cast<const R*>(gram), t1buf);
+    e = launch_pre2<R>(a, g, rd.count, D, gram, t1buf, st);
     E(TD_K_PRE);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     B(TD_K_GRAM);
     k_gram<T, R><<<dim3(2 * rd.count, a.B), 256, smem_g, st>>>(a, g, reinterpret_cast<R*>(gram), t1buf);
@@ -553,15 +335,9 @@ cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round&
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const size_t smem_c = core_smem_bytes(D);
-  if (smem_c > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_core<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
-    if (e != cudaSuccess) return e;
-  }
   B(TD_K_CORE);
-  k_core<R><<<dim3(rd.count, a.B), 128, smem_c, st>>>(a, g, reinterpret_cast<const R*>(gram), tbuf, S, t1buf);
+  e = launch_core2<R>(a, g, rd.count, D, gram, tbuf, t1buf, S, /*precond=*/sizeof(R) == 4, st);
   E(TD_K_CORE);
-  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int tiles = (rd.max_rows + kUpdRows - 1) / kUpdRows;
   const size_t smem_u = sizeof(R) * (2 * D * Dn + 2 * kUpdRows * D);

@@ -27,10 +27,14 @@ struct FinalArgs {
   double* logacc;
   const FinalSite* sites;
   const int32_t* grid_site;  // [ny][nx]
-  void* scratch;             // [B][scratch_elems] of the accumulation type
+  void* scratch;             // [B][scratch_elems] of the accumulation type (global)
   double* Z;                 // [B][2]
   int64_t scratch_elems;
-  int64_t off_mps0, off_mps1, mps_stride, off_C0, off_C1, off_F, off_T1, off_T, off_G, off_V, off_s;
+  int64_t off_mps0, off_mps1, mps_stride;   // boundary MPS (global scratch)
+  int64_t off_work;          // work region in the global scratch (when not in shared memory)
+  int64_t work_elems;        // work region size (elements)
+  int64_t w_F, w_W, w_MT, w_C0, w_C1, w_s, w_ord;   // offsets inside the work region
+  int32_t use_smem;          // work region in dynamic shared memory
   int32_t nbonds, chi, nslots, slot;
   int32_t nx, ny, chi_mps;
   int32_t B;
@@ -66,7 +70,15 @@ template <typename T, typename R>
 cudaError_t launch_final(const FinalArgs& f, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st);
 
-size_t core_smem_bytes(int D);
+// Truncation cores (core.cu): refinement factor of the first FP32 Gram (k_pre) and the
+// simple-update core (k_core); Dm = the round's largest active bond dimension.
+template <typename R>
+cudaError_t launch_pre2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* t1buf,
+                        cudaStream_t st);
+template <typename R>
+cudaError_t launch_core2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* tbuf,
+                         const double* t1buf, int S, bool precond, cudaStream_t st);
+size_t core2_smem_bytes(int Dm);
 
 // Static scratch of the allocation-free final contraction (final.cu).
 constexpr size_t kStaticFinalScratchBytes = size_t(64) << 20;   // 64 MiB

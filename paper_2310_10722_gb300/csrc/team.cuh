@@ -1,0 +1,295 @@
+// Team-cooperative dense linear algebra for the small FP64/FP32 factorisations of the
+// sweep (Sec. 4 simple-update truncation) and of the final boundary-MPS contraction.
+//
+// A team is a group of nt threads of one block (nt = 32: one warp, synchronised with
+// __syncwarp; nt a larger multiple of 32: its own named barrier).  Several teams share a
+// block, each working on an independent problem, so no step waits on a block-wide barrier.
+//
+// Methods (textbook, written for this layout):
+//   * pivoted Cholesky of a positive semi-definite Gram matrix (Golub & Van Loan,
+//     Matrix Computations, 4th ed., Alg. 4.2.4 with diagonal pivoting, Sec. 4.2.8), stopped
+//     at the first pivot below a tolerance: a rank-revealing R factor of the Gram's matrix;
+//   * the inverse of the triangular part by back substitution (ibid. Sec. 3.1);
+//   * the one-sided (Hestenes) Jacobi SVD with the round-robin parallel ordering
+//     (ibid. Sec. 8.6.3 and 8.5.5): the n/2 column pairs of one step are disjoint, so each
+//     pair is handled by its own group of g lanes, which computes the pair's three inner
+//     products (lane partial sums combined by shuffles), the rotation (the symmetric 2x2
+//     Schur rotation, ibid. Alg. 8.5.1), and applies it to both columns of A and of V.
+//     One barrier per step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace td {
+
+struct Team {
+  int tid;   // thread index inside the team
+  int nt;    // team size: 32, or a multiple of 32 using named barrier `bar`
+  int bar;   // named barrier id (1..15), unused for nt == 32
+  __device__ __forceinline__ void sync() const {
+    if (nt == 32)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+  }
+};
+
+template <typename R>
+struct TeamTol;
+template <>
+struct TeamTol<double> {
+  static __device__ __forceinline__ double rel() { return 1e-15; }
+  static __device__ __forceinline__ double tiny() { return 1e-290; }
+};
+template <>
+struct TeamTol<float> {
+  static __device__ __forceinline__ float rel() { return 1e-7f; }
+  static __device__ __forceinline__ float tiny() { return 1e-30f; }
+};
+
+// Pair i of step k of the round-robin ("circle") ordering of ne (even) players; player
+// ne-1 stays in place.  p < q on return.
+__device__ __forceinline__ void team_rr_pair(int k, int i, int ne, int& p, int& q) {
+  const int m = ne - 1;
+  if (i == 0) {
+    p = k;
+    q = m;
+  } else {
+    p = (k + i) % m;
+    q = (k - i + m) % m;
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Pivoted Cholesky of the symmetric positive semi-definite D x D matrix G (row-major,
+// leading dimension ldg; destroyed), D <= 32.  Pivot k is the largest remaining diagonal
+// entry; the factorisation stops when it is <= tol.  On return rows 0..r-1 of Rf (ld ldr)
+// hold the factor in the original column order -- G ~= Rf^T Rf, Rf[i][piv[j]] = 0 for
+// j < i -- and piv[0..r) the pivot columns.  `shr` is 2 ints of team-shared scratch.
+// Returns the rank r.
+template <typename R>
+__device__ int team_pchol(const Team& tm, R* G, int ldg, int D, R tol, R* Rf, int ldr, int* piv, int* shr) {
+  uint32_t done = 0;
+  int r = 0;
+  for (int k = 0; k < D; ++k) {
+    if (tm.tid < 32) {
+      const int lane = tm.tid;
+      R v = (lane < D && !((done >> lane) & 1u)) ? G[lane * ldg + lane] : R(-1);
+      int idx = lane;
+      for (int o = 16; o > 0; o >>= 1) {
+        const R v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (v2 > v || (v2 == v && i2 < idx)) {
+          v = v2;
+          idx = i2;
+        }
+      }
+      if (lane == 0) {
+        shr[0] = idx;
+        shr[1] = (v > tol) ? 1 : 0;
+      }
+    }
+    tm.sync();
+    const int p = shr[0];
+    if (!shr[1]) break;
+    const R rkk = sqrt(G[p * ldg + p]);
+    const R inv = R(1) / rkk;
+    for (int c = tm.tid; c < D; c += tm.nt) {
+      R v;
+      if (c == p)
+        v = rkk;
+      else if ((done >> c) & 1u)
+        v = R(0);
+      else
+        v = G[p * ldg + c] * inv;
+      Rf[k * ldr + c] = v;
+    }
+    if (tm.tid == 0) piv[k] = p;
+    done |= 1u << p;
+    tm.sync();
+    for (int w = tm.tid; w < D * D; w += tm.nt) {
+      const int a = w / D, c = w % D;
+      if (((done >> a) & 1u) || ((done >> c) & 1u)) continue;
+      G[a * ldg + c] -= Rf[k * ldr + a] * Rf[k * ldr + c];
+    }
+    tm.sync();
+    r = k + 1;
+  }
+  return r;
+}
+
+// Right inverse of the pivoted factor: Ri (D x r, ld ldi) with Rf Ri = I_r, nonzero only
+// in the pivot rows: Ri[piv[i]][j] = (R11^-1)[i][j], R11[i][j] = Rf[i][piv[j]] upper
+// triangular.  One column of R11^-1 per thread, by back substitution.
+template <typename R>
+__device__ void team_pchol_rinv(const Team& tm, const R* Rf, int ldr, const int* piv, int r, int D, R* Ri,
+                                int ldi) {
+  for (int w = tm.tid; w < D * r; w += tm.nt) Ri[(w / r) * ldi + (w % r)] = R(0);
+  tm.sync();
+  for (int j = tm.tid; j < r; j += tm.nt) {
+    Ri[piv[j] * ldi + j] = R(1) / Rf[j * ldr + piv[j]];
+    for (int i = j - 1; i >= 0; --i) {
+      R s = R(0);
+      for (int l = i + 1; l <= j; ++l) s += Rf[i * ldr + piv[l]] * Ri[piv[l] * ldi + j];
+      Ri[piv[i] * ldi + j] = -s / Rf[i * ldr + piv[i]];
+    }
+  }
+  tm.sync();
+}
+
+// Rotation (c, s) of the one-sided Jacobi step for columns with squared norms al, be and
+// inner product ga; false when the pair is already orthogonal to working precision
+// (ga^2 <= tol^2 al be), or when a column is negligible (squared norm below tiny(); FP32
+// solves run on matrices scaled to a largest entry of 1).
+template <typename R>
+__device__ __forceinline__ bool jacobi_rot(R al, R be, R ga, R& c, R& s) {
+  const R tol = TeamTol<R>::rel();
+  if (ga == R(0) || al <= TeamTol<R>::tiny() || be <= TeamTol<R>::tiny() || ga * ga <= tol * tol * (al * be)) {
+    c = R(1);
+    s = R(0);
+    return false;
+  }
+  const R zeta = (be - al) / (R(2) * ga);
+  const R t = (zeta >= R(0) ? R(1) : R(-1)) / (fabs(zeta) + sqrt(R(1) + zeta * zeta));
+  c = rsqrt(R(1) + t * t);
+  s = t * c;
+  return true;
+}
+
+// Largest power of two <= x (x >= 1).
+__device__ __forceinline__ int team_pow2_floor(int x) {
+  int g = 1;
+  while (2 * g <= x) g *= 2;
+  return g;
+}
+
+// One-sided Jacobi SVD of the m x n matrix A, stored column-major (element (r, c) at
+// A[c * lda + r]; an odd lda keeps the lanes of different column pairs on different shared
+// memory banks): on return the columns of A are mutually orthogonal, A_out = A_in V, with
+// V (n x n, column-major, ldv) orthogonal -- so the singular values are the column norms
+// of A_out and its normalised columns the left singular vectors.  With init_V false, V
+// holds an orthogonal matrix on entry and is updated as V <- V J.  `flag` is one int of
+// team-shared scratch.  Returns the number of sweeps.
+template <typename R>
+__device__ int team_svd_onesided(const Team& tm, R* A, int lda, int m, int n, R* V, int ldv, int* flag,
+                                 int max_sweeps, bool init_V = true) {
+  if (init_V)
+    for (int w = tm.tid; w < n * n; w += tm.nt) V[(w / n) * ldv + (w % n)] = (w / n == w % n) ? R(1) : R(0);
+  tm.sync();
+  if (n < 2) return 0;
+  const int ne = n + (n & 1), half = ne / 2;
+  int g = tm.nt / half;
+  g = g < 1 ? 1 : (g > 32 ? 32 : team_pow2_floor(g));
+  const int rows_max = m > n ? m : n;
+  while (g > 1 && g > rows_max) g >>= 1;
+  const int ngroups = tm.nt / g;
+  const int grp = tm.tid / g, gl = tm.tid % g;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tm.tid == 0) *flag = 0;
+    tm.sync();
+    for (int k = 0; k < ne - 1; ++k) {
+      for (int i0 = 0; i0 < half; i0 += ngroups) {
+        const int i = i0 + grp;
+        int p = 0, q = 0;
+        bool active = i < half;
+        if (active) {
+          team_rr_pair(k, i, ne, p, q);
+          active = q < n;
+        }
+        R* ap_ = A + (size_t)p * lda;
+        R* aq_ = A + (size_t)q * lda;
+        R al = R(0), be = R(0), ga = R(0);
+        if (active)
+          for (int r = gl; r < m; r += g) {
+            const R ap = ap_[r], aq = aq_[r];
+            al += ap * ap;
+            be += aq * aq;
+            ga += ap * aq;
+          }
+        for (int o = g >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        R c, s;
+        if (active && jacobi_rot(al, be, ga, c, s)) {
+          if (gl == 0) *flag = 1;
+          for (int r = gl; r < m; r += g) {
+            const R ap = ap_[r], aq = aq_[r];
+            ap_[r] = c * ap - s * aq;
+            aq_[r] = s * ap + c * aq;
+          }
+          R* vp_ = V + (size_t)p * ldv;
+          R* vq_ = V + (size_t)q * ldv;
+          for (int r = gl; r < n; r += g) {
+            const R vp = vp_[r], vq = vq_[r];
+            vp_[r] = c * vp - s * vq;
+            vq_[r] = s * vp + c * vq;
+          }
+        }
+      }
+      tm.sync();
+    }
+    const int any = *flag;
+    tm.sync();
+    if (!any) break;
+  }
+  return sweep;
+}
+
+// Column norms of A (m x n, column-major, lda): out[j] = ||A[:, j]||.
+template <typename R>
+__device__ void team_col_norms(const Team& tm, const R* A, int lda, int m, int n, R* out) {
+  for (int j = tm.tid; j < n; j += tm.nt) {
+    const R* a = A + (size_t)j * lda;
+    R s = R(0);
+    for (int r = 0; r < m; ++r) s += a[r] * a[r];
+    out[j] = sqrt(s);
+  }
+  tm.sync();
+}
+
+// Odd leading dimension >= rows (column-major storage without bank-aligned columns).
+__host__ __device__ __forceinline__ int odd_ld(int rows) { return rows | 1; }
+
+// Descending order of n non-negative values (ties: lower index first): order[rank] = j.
+// Ranks are counted on the bit patterns, which order non-negative IEEE values exactly.
+template <typename R>
+__device__ void team_sort_desc(const Team& tm, const R* v, int n, int* order) {
+  for (int j = tm.tid; j < n; j += tm.nt) {
+    const double vj = double(v[j]);
+    const long long bj = __double_as_longlong(vj);
+    int rank = 0;
+    for (int i = 0; i < n; ++i) {
+      const long long bi = __double_as_longlong(double(v[i]));
+      rank += (bi > bj || (bi == bj && i < j)) ? 1 : 0;
+    }
+    order[rank] = j;
+  }
+  tm.sync();
+}
+
+// Number of singular values kept: s (descending, s[0] > 0); at most chi, only those above
+// cutoff * s[0]; a cut inside a multiplet (s[k-1] - s[k] <= rtol * s[0]) drops it whole
+// unless that leaves nothing.
+template <typename R>
+__device__ __forceinline__ int team_keep_count(const R* s, int n, int chi, double cutoff, double rtol) {
+  int r = 0;
+  while (r < n && double(s[r]) > cutoff * double(s[0])) ++r;
+  int k = r < chi ? r : chi;
+  if (k < r) {
+    int kk = k;
+    while (kk > 0 && double(s[kk - 1]) - double(s[kk]) <= rtol * double(s[0])) --kk;
+    if (kk > 0) k = kk;
+  }
+  return k;
+}
+
+}  // namespace td
