@@ -33,9 +33,8 @@ struct td_network {
   void* d_gamma = nullptr;
   double* d_lam = nullptr;
   double* d_logacc = nullptr;
-  void* d_gram = nullptr;
+  double* d_gram = nullptr;
   double* d_tbuf = nullptr;
-  double* d_t1buf = nullptr;   // refinement transforms (FP32 storage only)
   void* d_fscr = nullptr;
   double* d_Z = nullptr;
   td::GateDesc* d_gates = nullptr;
@@ -164,8 +163,11 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   net->fin.off_work = net->fin.use_smem ? 0 : take(wacc);
   net->fin.scratch_elems = acc;
 
+  int max_chunks = 1;
+  for (const td::LayerPlan& L : P.layers)
+    for (const td::Round& rd : L.rounds) max_chunks = std::max(max_chunks, td::absorb_chunks(rd.max_rows, td::kChunkRows));
   const size_t per_shot = P.shot_elems * net->elem + (size_t)P.n_bonds * chi * 8 + (size_t)net->nslots * 8 +
-                          (size_t)P.max_round_gates * 4 * chi * chi * (net->elem + 8 + (o.precision == TD_FP64 ? 0 : 16)) +
+                          (size_t)P.max_round_gates * 4 * chi * chi * (8 * max_chunks + 8) +
                           (size_t)acc * net->elem + 16 + (size_t)P.n_det + 16;
   const size_t budget = o.mem_budget ? o.mem_budget : (size_t(16) << 30);
   int64_t wave = (int64_t)(budget / std::max<size_t>(per_shot, 1));
@@ -177,10 +179,8 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   bool ok = net->alloc(net->d_gamma, (size_t)wave * P.shot_elems * net->elem) &&
             net->alloc(net->d_lam, (size_t)wave * P.n_bonds * chi * 8) &&
             net->alloc(net->d_logacc, (size_t)wave * net->nslots * 8) &&
-            net->alloc(net->d_gram, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * net->elem) &&
+            net->alloc(net->d_gram, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * 8 * max_chunks) &&
             net->alloc(net->d_tbuf, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * 8) &&
-            (o.precision == TD_FP64 ||
-             net->alloc(net->d_t1buf, (size_t)std::max(P.max_round_gates, 1) * wave * 8 * chi * chi * 8)) &&
             net->alloc(net->d_fscr, (size_t)wave * acc * net->elem) &&
             net->alloc(net->d_Z, (size_t)wave * 2 * 8) &&
             net->alloc(net->d_gates, sizeof(td::GateDesc) * P.gates.size()) &&
@@ -199,7 +199,7 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
     return cuda_fail(e, "descriptor upload");
   }
   int64_t launches = 1 + 2;   // init, final, finalize
-  const int per_round = (o.precision == TD_FP64) ? 3 : 5;
+  const int per_round = 3;   // Gram, core, update
   for (const td::LayerPlan& L : P.layers) launches += 1 + per_round * (int64_t)L.rounds.size();
   net->launches_per_wave = launches;
   *out = net;
@@ -253,9 +253,8 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
       }
       if (e != cudaSuccess) return cuda_fail(e, "local launch");
       for (const td::Round& rd : L.rounds) {
-        e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, nullptr, P.S, st, &prof)
-                : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, net->d_t1buf, P.S, st,
-                                                 &prof);
+        e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, P.S, st, &prof)
+                : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, P.S, st, &prof);
         if (e != cudaSuccess) return cuda_fail(e, "gate round launch");
       }
     }
@@ -408,8 +407,8 @@ td_status td_debug_sweep(td_network* net, const uint8_t* det_dev, int64_t B, int
     if (e != cudaSuccess) return cuda_fail(e, "local launch");
     for (const td::Round& rd : L.rounds) {
       if (done >= n_gates) break;
-      e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, nullptr, P.S, st)
-              : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, net->d_t1buf, P.S, st);
+      e = f64 ? td::launch_round<double, double>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, P.S, st)
+              : td::launch_round<float, float>(a, net->d_gates, rd, net->d_gram, net->d_tbuf, P.S, st);
       if (e != cudaSuccess) return cuda_fail(e, "gate round launch");
       done += rd.count;
     }
@@ -461,27 +460,23 @@ td_status td_network_get_work(const td_network* net, double* bytes, double* flop
   }
   for (const td::GateDesc& g : P.gates) {
     const double D = g.D, Dn = g.Dn;
-    for (int s = 0; s < 2; ++s) {
-      const td::SideDesc& sd = g.side[s];
+    for (int sd_i = 0; sd_i < 2; ++sd_i) {
+      const td::SideDesc& sd = g.side[sd_i];
       const double OI = (double)sd.outer * sd.inner;
       const double rows = sd.P / 2 * OI;
       const double in = sd.P * OI * D * el, out = sd.P * OI * Dn * el;
-      const int passes = f64 ? 1 : 2;
-      bytes[TD_K_GRAM] += passes * in;
-      flops[TD_K_GRAM] += passes * 2.0 * rows * 2.0 * D * D + (f64 ? 0.0 : 2.0 * rows * 2.0 * D * D);
-      if (f64) fp64_flops[TD_K_GRAM] += 2.0 * rows * 2.0 * D * D;
+      bytes[TD_K_GRAM] += in;
+      flops[TD_K_GRAM] += 2.0 * rows * 2.0 * D * D;               // G+ and G-, FP64 accumulation
+      fp64_flops[TD_K_GRAM] += 2.0 * rows * 2.0 * D * D;
       bytes[TD_K_UPDATE] += in + out;
-      flops[TD_K_UPDATE] += 2.0 * rows * 2.0 * D * Dn;
+      flops[TD_K_UPDATE] += 2.0 * rows * 2.0 * D * Dn;            // Y T+ and Z T-
       if (f64) fp64_flops[TD_K_UPDATE] += 2.0 * rows * 2.0 * D * Dn;
     }
-    if (!f64) {
-      flops[TD_K_PRE] += 4.0 * eig(D);
-      fp64_flops[TD_K_PRE] += 4.0 * eig(D);
-    }
-    const double core = 4.0 * eig(D) + svd(2 * D, 2 * D) + 2.0 * 4.0 * D * D * D + 2.0 * 4.0 * D * Dn * 2 * D;
+    // four pivoted Cholesky factors and triangular inverses, theta, SVD, transforms
+    const double core = 8.0 * D * D * D / 3.0 + 8.0 * D * D * D + svd(2 * D, 2 * D) + 2.0 * 4.0 * D * Dn * 2 * D;
     flops[TD_K_CORE] += core;
     fp64_flops[TD_K_CORE] += core;
-    bytes[TD_K_CORE] += 4.0 * D * D * (f64 ? 8 : 4) + 4.0 * D * Dn * 8;
+    bytes[TD_K_CORE] += 4.0 * D * D * 8 + 4.0 * D * Dn * 8;
   }
   // final contraction: zip-up with static dims, kept bond min(chi_mps, m, n) at every cut
   std::vector<double> mL(P.nx, 1), mDn(P.nx, 1), mR(P.nx, 1);

@@ -11,16 +11,15 @@
 // the update transforms T_{X kappa} = R_{X kappa}^+ [U or V]_{kappa rows, :k} / sqrt2 are
 // written for k_update.
 //
-// FP32 storage refines the R factors once (an eigen-free CholeskyQR2 with a shift): k_pre
-// factors the first FP32 Gram plus a shift of kPreFloor of the side's largest diagonal,
-// R1, and emits T1 = R1^-1 and R1; k_gram then forms the Gram of Q1 = M T1, whose pivoted
-// Cholesky R2 gives R = R2 R1 and R^+ = T1 R2^+.
+// The Gram blocks arrive in FP64 on both paths (summed in FP64 from the stored tensors).
 //
 // The SVD of theta is FP64 one-sided Jacobi.  With `precond` (the mixed-precision path) it
 // is first solved in FP32 on a scaled copy; the FP32 right factor, re-orthogonalised in
 // FP64 by one Newton-Schulz step V <- V (3I - V^T V)/2, preconditions the FP64 Jacobi
-// sweeps, which then converge in one or two sweeps (mixed-precision Jacobi: precondition
-// with a low-precision factor, finish in high precision).
+// sweeps, which are run to convergence (mixed-precision Jacobi: precondition with a
+// low-precision factor, finish in high precision).  The FP32 solve cannot resolve singular
+// values below ~1e-7 of the largest, and the simple update is sensitive to the ones it keeps
+// down to the cutoff, so the FP64 sweeps are not cut short.
 #include <cfloat>
 #include <cmath>
 
@@ -29,19 +28,18 @@
 
 namespace td {
 
-constexpr double kPreFloor = 1e-6;
-
 // Team-shared layout of one item (doubles): five regions of regsz(Dm) = 2Dm x (2Dm + 1)
 // (a 2Dm x 2Dm matrix with an odd leading dimension) plus small arrays.
 struct CoreSmem {
   double* reg[5];
   double* lam;     // [Dm]
   double* sv;      // [2Dm]
+  double* aux;     // [4][Dm] reciprocal Cholesky diagonals, then [2Dm] reciprocal singular values
   int* piv;        // [4][Dm]
   int* order;      // [2Dm]
   int* meta;       // [16]
   static __host__ __device__ size_t regsz(int Dm) { return 4 * (size_t)Dm * Dm + 2 * (size_t)Dm + 2; }
-  static __host__ __device__ size_t doubles(int Dm) { return 5 * regsz(Dm) + 3 * (size_t)Dm + 8; }
+  static __host__ __device__ size_t doubles(int Dm) { return 5 * regsz(Dm) + 7 * (size_t)Dm + 8; }
   static __host__ __device__ size_t ints(int Dm) { return 6 * (size_t)Dm + 16; }
   static __host__ __device__ size_t bytes(int Dm) { return doubles(Dm) * 8 + ints(Dm) * 4 + 16; }
   __device__ void carve(unsigned char* base, int Dm) {
@@ -49,7 +47,8 @@ struct CoreSmem {
     for (int i = 0; i < 5; ++i) reg[i] = d + (size_t)i * regsz(Dm);
     lam = d + 5 * regsz(Dm);
     sv = lam + Dm;
-    int* ip = reinterpret_cast<int*>(sv + 2 * Dm + 8);
+    aux = sv + 2 * Dm + 8;
+    int* ip = reinterpret_cast<int*>(aux + 4 * Dm);
     piv = ip;
     order = piv + 4 * Dm;
     meta = order + 2 * Dm;
@@ -150,68 +149,22 @@ __device__ void svd_precond(const Team& tm, double* A, int lda, int m, int n, do
   team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, false);
 }
 
-// Refinement step 1 (FP32 storage): shifted Cholesky of the four first-pass Gram blocks.
-// t1buf block layout: [T1 = R1^-1 (D x D)][R1 (D x D)] at stride chi*chi.
-template <typename R>
-__global__ void k_pre2(SweepArgs a, const GateDesc* __restrict__ gates, const R* __restrict__ gram,
-                       double* __restrict__ t1buf, int n_items, int team_threads, int Dm) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Team tm = make_team(team_threads);
-  const int team = threadIdx.x / team_threads;
-  const int64_t item = (int64_t)blockIdx.x * (blockDim.x / team_threads) + team;
-  if (item >= n_items) return;
-  CoreSmem sm;
-  sm.carve(smem_raw + (size_t)team * CoreSmem::bytes(Dm), Dm);
-  const int gi = (int)(item / a.B), b = (int)(item % a.B);
-  const int D = gates[gi].D, chi = a.chi, DD = D * D;
-  const R* gsrc = gram + item * 4 * chi * chi;
-  double* G = sm.reg[0];
-  double* Rf = sm.reg[1];
-  double* Ri = sm.reg[2];
-  for (int w = tm.tid; w < 4 * DD; w += tm.nt) G[w] = double(gsrc[(int64_t)(w / DD) * chi * chi + w % DD]);
-  tm.sync();
-  double ref[2];
-  for (int side = 0; side < 2; ++side) {
-    double e = 0.0;
-    for (int blk = 2 * side; blk < 2 * side + 2; ++blk)
-      for (int j = 0; j < D; ++j) e = fmax(e, G[blk * DD + j * D + j]);
-    ref[side] = e;
-  }
-  double* out = t1buf + item * 4 * 2 * chi * chi;
-  for (int blk = 0; blk < 4; ++blk) {
-    const double rf = ref[blk / 2];
-    double* T1 = out + (int64_t)blk * 2 * chi * chi;
-    double* R1 = T1 + chi * chi;
-    int r = 0;
-    if (rf > 0.0) {
-      const double shift = kPreFloor * rf;
-      for (int j = tm.tid; j < D; j += tm.nt) G[blk * DD + j * D + j] += shift;
-      tm.sync();
-      r = team_pchol<double>(tm, G + blk * DD, D, D, 0.5 * shift, Rf + blk * DD, D, sm.piv + blk * Dm, sm.meta);
-    }
-    if (r == D) {
-      team_pchol_rinv<double>(tm, Rf + blk * DD, D, sm.piv + blk * Dm, D, D, Ri + blk * DD, D);
-      for (int w = tm.tid; w < DD; w += tm.nt) {
-        T1[w] = Ri[blk * DD + w];
-        R1[w] = Rf[blk * DD + w];
-      }
-    } else {
-      // zero side (or a rounding breakdown): a plain scaling keeps T1 invertible
-      const double s = rf > 0.0 ? sqrt(rf) : 1.0;
-      for (int w = tm.tid; w < DD; w += tm.nt) {
-        const bool dg = (w / D) == (w % D);
-        T1[w] = dg ? 1.0 / s : 0.0;
-        R1[w] = dg ? s : 0.0;
-      }
-    }
-    tm.sync();
+// The four Gram blocks of item (gate, shot) in FP64: the sum, in chunk order, of the
+// partial Grams of its row chunks.
+__device__ __forceinline__ void load_gram(const Team& tm, const double* gram, int64_t item, int nchunk, int chi,
+                                          int D, double* G) {
+  const int DD = D * D;
+  const double* src = gram + item * nchunk * 4 * chi * chi;
+  for (int w = tm.tid; w < 4 * DD; w += tm.nt) {
+    const int64_t off = (int64_t)(w / DD) * chi * chi + w % DD;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += src[(int64_t)c * 4 * chi * chi + off];
+    G[w] = s;
   }
 }
 
-template <typename R>
-__global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R* __restrict__ gram,
-                        double* __restrict__ tbuf, int S, const double* __restrict__ t1buf, int n_items,
-                        int team_threads, int Dm, int precond) {
+__global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const double* __restrict__ gram,
+                        double* __restrict__ tbuf, int S, int n_items, int team_threads, int Dm, int precond) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Team tm = make_team(team_threads);
   const int team = threadIdx.x / team_threads;
@@ -224,63 +177,33 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R
   const int D = gd.D, Dn = gd.Dn, chi = a.chi, DD = D * D;
   int* meta = sm.meta;
   double* slot = reinterpret_cast<double*>(sm.sv + 2 * Dm);   // one spare double after sv
-  const R* gsrc = gram + item * 4 * chi * chi;
   double* RG = sm.reg[0];
   double* RF = sm.reg[1];
   double* RI = sm.reg[2];
   double* TH = sm.reg[3];
   double* VV = sm.reg[4];
-  for (int w = tm.tid; w < 4 * DD; w += tm.nt) RG[w] = double(gsrc[(int64_t)(w / DD) * chi * chi + w % DD]);
+  load_gram(tm, gram, item, a.gram_chunks, chi, D, RG);
   double* lamg = a.lam + ((int64_t)b * a.nbonds + gd.bond) * chi;
   for (int w = tm.tid; w < D; w += tm.nt) sm.lam[w] = lamg[w];
   tm.sync();
-  double tolv[2];
-  for (int side = 0; side < 2; ++side) {
+  // pivot tolerance per block: gram_cutoff times the side's largest diagonal (< 0: empty)
+  if (tm.tid < 4) {
+    const int side = tm.tid / 2;
     double e = 0.0;
     for (int blk = 2 * side; blk < 2 * side + 2; ++blk)
       for (int j = 0; j < D; ++j) e = fmax(e, RG[blk * DD + j * D + j]);
-    tolv[side] = e;
-  }
-  int rk[4];
-  for (int blk = 0; blk < 4; ++blk) {
-    const double e = tolv[blk / 2];
-    rk[blk] = 0;
-    if (e > 0.0)
-      rk[blk] = team_pchol<double>(tm, RG + blk * DD, D, D, a.gram_cutoff * e, RF + blk * DD, D,
-                                   sm.piv + blk * Dm, meta);
-    if (rk[blk] > 0) team_pchol_rinv<double>(tm, RF + blk * DD, D, sm.piv + blk * Dm, rk[blk], D, RI + blk * DD, D);
+    sm.sv[tm.tid] = e > 0.0 ? a.gram_cutoff * e : -1.0;
   }
   tm.sync();
-  const double* Rm = RF;     // R factor rows (r x D, ld D) per block
+  int* rkp = meta + 12;
+  team_pchol4(tm, RG, D, DD, sm.sv, RF, sm.piv, sm.aux, Dm, rkp);
+  team_pchol_rinv4(tm, RF, D, DD, sm.piv, sm.aux, Dm, rkp, RI);
+  int rk[4];
+  for (int blk = 0; blk < 4; ++blk) rk[blk] = rkp[blk];
+  double* Rm = RF;           // R factor rows (r x D, ld D) per block
   const double* Rinv = RI;   // right inverse (D x r, ld D) per block
-  double* FF = RG;           // scratch free during the SVD
-  double* TT = RF;
-  if (t1buf) {
-    // R = R2 R1 (R1 = T1^-1) into RG, R^+ = T1 R2^+ into RF
-    const double* t1 = t1buf + item * 4 * 2 * chi * chi;
-    for (int w = tm.tid; w < 4 * DD; w += tm.nt) {
-      const int blk = w / DD, e = w % DD;
-      TH[w] = t1[(int64_t)blk * 2 * chi * chi + chi * chi + e];   // R1
-      VV[w] = t1[(int64_t)blk * 2 * chi * chi + e];               // T1
-    }
-    tm.sync();
-    for (int blk = 0; blk < 4; ++blk) {
-      const int r = rk[blk];
-      if (r == 0) continue;
-      team_gemm<double>(tm, RF + blk * DD, D, TH + blk * DD, D, RG + blk * DD, D, r, D, D);
-    }
-    tm.sync();
-    for (int blk = 0; blk < 4; ++blk) {
-      const int r = rk[blk];
-      if (r == 0) continue;
-      team_gemm<double>(tm, VV + blk * DD, D, RI + blk * DD, D, RF + blk * DD, D, D, r, D);
-    }
-    tm.sync();
-    Rm = RG;
-    Rinv = RF;
-    FF = RI;
-    TT = RG;
-  }
+  double* FF = RG;           // scratch free during the SVD (the Gram is consumed)
+  double* TT = RF;           // scratch free once theta is formed (R is consumed)
   const int rAp = rk[0], rA = rk[0] + rk[1], rBp = rk[2], rB = rk[2] + rk[3];
   double* tout = tbuf + item * 4 * chi * chi;
   if (rA == 0 || rB == 0) {            // zero state: this shot has probability 0
@@ -291,7 +214,13 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R
   }
   const double p = gd.p;
   const double cpp = 0.5, cpm = 0.5 * (1.0 - 2.0 * p);
-  // theta[i][j] = c(ki, kj) sum_q R_{A ki}[li][q] lambda_q R_{B kj}[lj][q]  (column-major)
+  for (int w = tm.tid; w < rA * D; w += tm.nt) {     // R_A Lambda, in place
+    const int i = w / D, q = w % D;
+    const int ka = i < rAp ? 0 : 1, li = i - ka * rAp;
+    Rm[ka * DD + li * D + q] *= sm.lam[q];
+  }
+  tm.sync();
+  // theta[i][j] = c(ki, kj) sum_q (R_{A ki} Lambda)[li][q] R_{B kj}[lj][q]  (column-major)
   const int ldt = odd_ld(rA), ldv = odd_ld(rB);
   for (int w = tm.tid; w < rA * rB; w += tm.nt) {
     const int j = w / rA, i = w % rA;
@@ -300,7 +229,7 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R
     const double* ra = Rm + ka * DD + li * D;
     const double* rb = Rm + (2 + kb) * DD + lj * D;
     double s = 0.0;
-    for (int q = 0; q < D; ++q) s += ra[q] * sm.lam[q] * rb[q];
+    for (int q = 0; q < D; ++q) s += ra[q] * rb[q];
     TH[j * ldt + i] = (ka == kb ? cpp : cpm) * s;
   }
   tm.sync();
@@ -326,6 +255,8 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R
     if (tm.tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] = -INFINITY;
     return;
   }
+  for (int j = tm.tid; j < k; j += tm.nt) sm.aux[j] = 1.0 / sm.sv[sm.order[j]];
+  tm.sync();
   const double rs2 = 0.70710678118654752440;
   // T_{A kap}[q][j] = sum_{li} R^+_{A kap}[q][li] U[kap rows li][order j] / sqrt2, U = theta_out / s
   for (int w = tm.tid; w < 2 * D * Dn; w += tm.nt) {
@@ -337,7 +268,7 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R
       const double* ri = Rinv + kap * DD + q * D;
       const double* u = TH + cj * ldt + off;
       for (int li = 0; li < r; ++li) acc += ri[li] * u[li];
-      acc /= sm.sv[cj];
+      acc *= sm.aux[j];
     }
     tout[(int64_t)kap * chi * chi + q * Dn + j] = acc * rs2;
   }
@@ -353,13 +284,15 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const R
     }
     tout[(int64_t)(2 + kap) * chi * chi + q * Dn + j] = acc * rs2;
   }
-  for (int j = tm.tid; j < Dn; j += tm.nt) lamg[j] = (j < k) ? sm.sv[sm.order[j]] / s0 : 0.0;
+  const double is0 = sm.aux[0];
+  for (int j = tm.tid; j < Dn; j += tm.nt) lamg[j] = (j < k) ? sm.sv[sm.order[j]] * is0 : 0.0;
   if (tm.tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] += log(s0);
 }
 
 // ---- launch configuration ---------------------------------------------------------------
 // Team size by bond dimension: small cores get one warp each (8 per block), larger ones a
-// group of warps, so that no block-wide barrier serialises independent gates.
+// group of warps, so that no block-wide barrier serialises independent gates.  The team is
+// split into four segments of at least Dm lanes for the four Cholesky factorisations.
 static void core_shape(int Dm, int& team_threads, int& teams) {
   if (Dm <= 8) { team_threads = 32; teams = 8; }
   else if (Dm <= 16) { team_threads = 64; teams = 2; }
@@ -373,41 +306,22 @@ size_t core2_smem_bytes(int Dm) {
 }
 
 template <typename R>
-cudaError_t launch_core2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* tbuf,
-                         const double* t1buf, int S, bool precond, cudaStream_t st) {
+cudaError_t launch_core2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const double* gram, double* tbuf,
+                         int S, bool precond, cudaStream_t st) {
   int tt, teams;
   core_shape(Dm, tt, teams);
   const int64_t n_items = (int64_t)count * a.B;
   const size_t smem = (size_t)teams * CoreSmem::bytes(Dm);
-  cudaError_t e = cudaFuncSetAttribute(k_core2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_core2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((n_items + teams - 1) / teams);
-  k_core2<R><<<blocks, tt * teams, smem, st>>>(a, g, reinterpret_cast<const R*>(gram), tbuf, S, t1buf,
-                                                (int)n_items, tt, Dm, precond ? 1 : 0);
+  k_core2<<<blocks, tt * teams, smem, st>>>(a, g, gram, tbuf, S, (int)n_items, tt, Dm, precond ? 1 : 0);
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_pre2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* t1buf,
-                        cudaStream_t st) {
-  int tt, teams;
-  core_shape(Dm, tt, teams);
-  const int64_t n_items = (int64_t)count * a.B;
-  const size_t smem = (size_t)teams * CoreSmem::bytes(Dm);
-  cudaError_t e = cudaFuncSetAttribute(k_pre2<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)((n_items + teams - 1) / teams);
-  k_pre2<R><<<blocks, tt * teams, smem, st>>>(a, g, reinterpret_cast<const R*>(gram), t1buf, (int)n_items, tt, Dm);
-  return cudaGetLastError();
-}
-
-template cudaError_t launch_core2<double>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
-                                          const double*, int, bool, cudaStream_t);
-template cudaError_t launch_core2<float>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
-                                         const double*, int, bool, cudaStream_t);
-template cudaError_t launch_pre2<float>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
-                                        cudaStream_t);
-template cudaError_t launch_pre2<double>(const SweepArgs&, const GateDesc*, int, int, const void*, double*,
-                                         cudaStream_t);
+template cudaError_t launch_core2<double>(const SweepArgs&, const GateDesc*, int, int, const double*, double*, int,
+                                          bool, cudaStream_t);
+template cudaError_t launch_core2<float>(const SweepArgs&, const GateDesc*, int, int, const double*, double*, int,
+                                         bool, cudaStream_t);
 
 }  // namespace td

@@ -136,7 +136,7 @@ __global__ void k_final(FinalArgs fa) {
       const int m = cJ * U, n = aR * Rr * 2;
       const int ldm = odd_ld(n), ldv = odd_ld(m);
       for (int w = tm.tid; w < m * n; w += tm.nt) {
-        const int ju = w / n, c = w % n;
+        const int c = w / m, ju = w % m;      // consecutive lanes: consecutive u (F) and ju (MT)
         const int q = c % 2, r = (c / 2) % Rr, bb = c / (2 * Rr);
         const int j = ju / U, u = ju % U;
         R acc = R(0);
@@ -177,8 +177,10 @@ __global__ void k_final(FinalArgs fa) {
           if (tm.tid == 0) { mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = 1; }
           cJ = 1;
         } else {
-          const R s0 = sv[ord[0]];
-          const R inv0 = R(1) / s0;
+          // exact power-of-two normalisation of the carry (its log to the log-scale)
+          int e2 = 0;
+          frexp(double(sv[ord[0]]), &e2);
+          const R inv0 = R(ldexp(1.0, -e2));
           for (int w = tm.tid; w < m * k; w += tm.nt) {
             const int ju = w / k, kk = w % k;
             An[w] = V[ord[kk] * ldv + ju];
@@ -188,7 +190,7 @@ __global__ void k_final(FinalArgs fa) {
             Cn[w] = MT[ord[kk] * ldm + c] * inv0;
           }
           if (tm.tid == 0) {
-            logsum_s += log((double)s0);
+            logsum_s += double(e2) * 0.69314718055994530942;
             mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = k;
           }
           cJ = k;
@@ -222,17 +224,21 @@ __global__ void k_final(FinalArgs fa) {
           for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
           if (tm.tid == 0) {
             meta[1] = 0;
-            if (mx > R(0)) logsum_s += log((double)mx); else logsum_s = -INFINITY;
-            slam[0] = mx;
+            int e2 = 0;
+            if (mx > R(0)) {
+              frexp(double(mx), &e2);
+              logsum_s += double(e2) * 0.69314718055994530942;
+            } else {
+              logsum_s = -INFINITY;
+            }
+            slam[0] = mx > R(0) ? R(ldexp(1.0, -e2)) : R(0);
             mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = 2;
           }
         }
         tm.sync();
-        const R mx = slam[0];
-        if (mx > R(0)) {
-          const R inv = R(1) / mx;
+        const R inv = slam[0];
+        if (inv > R(0))
           for (int w = tm.tid; w < m * 2; w += tm.nt) An[w] *= inv;
-        }
         tm.sync();
       }
     }

@@ -105,9 +105,9 @@ td_status build_plan(const td_dem& dem, const td_layout& layout, const td_option
   plan.n_det = n_det; plan.n_mech = n_mech; plan.n_obs = dem.n_obs;
   plan.chi = opt.chi; plan.chi_mps = opt.chi_mps; plan.precision = opt.precision;
   plan.svd_cutoff = opt.svd_cutoff; plan.multiplet_rtol = opt.multiplet_rtol;
-  // Gram eigen-directions below this fraction of the largest are rounding noise: FP64
-  // Grams resolve ~1e-16 of the largest eigenvalue, the refined FP32 Gram ~1e-7.
-  plan.gram_cutoff = opt.gram_cutoff >= 0 ? opt.gram_cutoff : (opt.precision == TD_FP64 ? 1e-15 : 1e-7);
+  // Gram directions below this fraction of the side's largest diagonal are rounding noise
+  // of the FP64 sums (both storage types accumulate the Gram in FP64).
+  plan.gram_cutoff = opt.gram_cutoff >= 0 ? opt.gram_cutoff : 1e-15;
   std::set<std::pair<int32_t, int32_t>> yx;
   int32_t T = 0;
   for (int32_t i = 0; i < n_det; ++i) {

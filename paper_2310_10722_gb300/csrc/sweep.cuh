@@ -17,6 +17,7 @@ struct SweepArgs {
   int32_t nbonds, chi, nslots, n_det;
   int32_t wave_first;       // first shot of this wave in `det`
   int32_t B;                // shots in this wave
+  int32_t gram_chunks;      // partial Grams per (gate, shot) of the current round (row chunks)
   double gram_cutoff, svd_cutoff, multiplet_rtol;
 };
 
@@ -64,21 +65,29 @@ cudaError_t launch_sweep_init(const SweepArgs& a, const LocalDesc* locals0, int 
 template <typename T, typename R>
 cudaError_t launch_local(const SweepArgs& a, const LocalDesc* locals, int S, cudaStream_t st);
 template <typename T, typename R>
-cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round& rd, void* gram, double* tbuf,
-                         double* t1buf, int S, cudaStream_t st, Prof* prof = nullptr);
+cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round& rd, double* gram, double* tbuf, int S,
+                         cudaStream_t st, Prof* prof = nullptr);
 template <typename T, typename R>
 cudaError_t launch_final(const FinalArgs& f, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st);
 
-// Truncation cores (core.cu): refinement factor of the first FP32 Gram (k_pre) and the
-// simple-update core (k_core); Dm = the round's largest active bond dimension.
+// Truncation core (core.cu): the simple-update core of every gate of a round; Dm = the
+// round's largest active bond dimension; gram: FP64 partial Grams.
 template <typename R>
-cudaError_t launch_pre2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* t1buf,
-                        cudaStream_t st);
-template <typename R>
-cudaError_t launch_core2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const void* gram, double* tbuf,
-                         const double* t1buf, int S, bool precond, cudaStream_t st);
+cudaError_t launch_core2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const double* gram, double* tbuf,
+                         int S, bool precond, cudaStream_t st);
 size_t core2_smem_bytes(int Dm);
+
+// Gram and update passes (absorb.cu), one warp per (gate side, shot, chunk of kChunkRows
+// rows); Dm = the round's largest bond dimension (before or after the gate).
+constexpr int kChunkRows = 2048;
+int absorb_chunks(int max_rows, int chunk_rows);
+template <typename T>
+cudaError_t launch_gram2(const SweepArgs& a, const GateDesc* g, int count, int Dm, double* gram, int nchunk,
+                         int chunk_rows, cudaStream_t st);
+template <typename T>
+cudaError_t launch_update2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const double* tbuf, int nchunk,
+                           int chunk_rows, cudaStream_t st);
 
 // Static scratch of the allocation-free final contraction (final.cu).
 constexpr size_t kStaticFinalScratchBytes = size_t(64) << 20;   // 64 MiB

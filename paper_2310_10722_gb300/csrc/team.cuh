@@ -143,13 +143,105 @@ __device__ void team_pchol_rinv(const Team& tm, const R* Rf, int ldr, const int*
   tm.sync();
 }
 
+// Four independent pivoted Cholesky factorisations (as team_pchol) run concurrently: the
+// team is split into four lane segments of seg = nt/4 lanes (D <= seg <= 32); segment b
+// factors the D x D block G + b*bstride into Rf + b*bstride (ld D), with its pivots and the
+// reciprocals of R11's diagonal (from one rsqrt per pivot) in piv/dinv + b*pstride and its
+// rank in rank[b] (team-shared).  tol[b] < 0 marks an empty block (rank 0).  Pivot
+// candidates are compared as bit patterns: non-negative doubles order as integers, and a
+// negative rounding residue loses to any admissible pivot.
+__device__ __forceinline__ void team_pchol4(const Team& tm, double* G, int D, int bstride, const double* tol,
+                                            double* Rf, int* piv, double* dinv, int pstride, int* rank) {
+  const int seg = tm.nt / 4;
+  const int blk = tm.tid / seg, sl = tm.tid % seg;
+  double* Gb = G + blk * bstride;
+  double* Rb = Rf + blk * bstride;
+  const double tl = tol[blk];
+  const long long tbits = __double_as_longlong(tl);
+  bool active = tl >= 0.0;
+  uint32_t done = 0;
+  int r = 0;
+  for (int k = 0; k < D; ++k) {
+    long long key = -1;
+    int idx = sl;
+    if (active && sl < D && !((done >> sl) & 1u)) key = __double_as_longlong(Gb[sl * D + sl]);
+    for (int o = seg >> 1; o > 0; o >>= 1) {
+      const long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (k2 > key || (k2 == key && i2 < idx)) {
+        key = k2;
+        idx = i2;
+      }
+    }
+    const bool ok = active && key > tbits;
+    const int p = idx;
+    if (ok) {
+      const double dpp = Gb[p * D + p];
+      const double inv = rsqrt(dpp);
+      const double rkk = dpp * inv;
+      for (int c = sl; c < D; c += seg) {
+        double v;
+        if (c == p)
+          v = rkk;
+        else if ((done >> c) & 1u)
+          v = 0.0;
+        else
+          v = Gb[p * D + c] * inv;
+        Rb[k * D + c] = v;
+      }
+      if (sl == 0) {
+        piv[blk * pstride + k] = p;
+        dinv[blk * pstride + k] = inv;
+      }
+      done |= 1u << p;
+      r = k + 1;
+    } else {
+      active = false;
+    }
+    tm.sync();
+    if (ok)
+      for (int w = sl; w < D * D; w += seg) {
+        const int a = w / D, c = w % D;
+        if (((done >> a) & 1u) || ((done >> c) & 1u)) continue;
+        Gb[a * D + c] -= Rb[k * D + a] * Rb[k * D + c];
+      }
+    tm.sync();
+  }
+  if (sl == 0) rank[blk] = r;
+  tm.sync();
+}
+
+// Right inverses of the four factors of team_pchol4 (as team_pchol_rinv, multiplying by
+// the stored reciprocal diagonals): Ri + b*bstride is D x r_b (ld D); one (block, column)
+// per thread.
+__device__ __forceinline__ void team_pchol_rinv4(const Team& tm, const double* Rf, int D, int bstride, const int* piv,
+                                                 const double* dinv, int pstride, const int* rank, double* Ri) {
+  for (int w = tm.tid; w < 4 * D * D; w += tm.nt) Ri[(w / (D * D)) * bstride + w % (D * D)] = 0.0;
+  tm.sync();
+  const int seg = tm.nt / 4;
+  const int blk = tm.tid / seg, j = tm.tid % seg;
+  const int r = rank[blk];
+  if (j < r) {
+    const double* Rb = Rf + blk * bstride;
+    double* Ib = Ri + blk * bstride;
+    const int* pb = piv + blk * pstride;
+    const double* db = dinv + blk * pstride;
+    Ib[pb[j] * D + j] = db[j];
+    for (int i = j - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1; l <= j; ++l) s += Rb[i * D + pb[l]] * Ib[pb[l] * D + j];
+      Ib[pb[i] * D + j] = -s * db[i];
+    }
+  }
+  tm.sync();
+}
+
 // Rotation (c, s) of the one-sided Jacobi step for columns with squared norms al, be and
 // inner product ga; false when the pair is already orthogonal to working precision
 // (ga^2 <= tol^2 al be), or when a column is negligible (squared norm below tiny(); FP32
 // solves run on matrices scaled to a largest entry of 1).
 template <typename R>
-__device__ __forceinline__ bool jacobi_rot(R al, R be, R ga, R& c, R& s) {
-  const R tol = TeamTol<R>::rel();
+__device__ __forceinline__ bool jacobi_rot(R al, R be, R ga, R tol, R& c, R& s) {
   if (ga == R(0) || al <= TeamTol<R>::tiny() || be <= TeamTol<R>::tiny() || ga * ga <= tol * tol * (al * be)) {
     c = R(1);
     s = R(0);
@@ -176,9 +268,11 @@ __device__ __forceinline__ int team_pow2_floor(int x) {
 // of A_out and its normalised columns the left singular vectors.  With init_V false, V
 // holds an orthogonal matrix on entry and is updated as V <- V J.  `flag` is one int of
 // team-shared scratch.  Returns the number of sweeps.
+// `tol`: convergence tolerance (<= 0: TeamTol<R>::rel()).
 template <typename R>
 __device__ int team_svd_onesided(const Team& tm, R* A, int lda, int m, int n, R* V, int ldv, int* flag,
-                                 int max_sweeps, bool init_V = true) {
+                                 int max_sweeps, bool init_V = true, R tol = R(0)) {
+  if (!(tol > R(0))) tol = TeamTol<R>::rel();
   if (init_V)
     for (int w = tm.tid; w < n * n; w += tm.nt) V[(w / n) * ldv + (w % n)] = (w / n == w % n) ? R(1) : R(0);
   tm.sync();
@@ -219,7 +313,7 @@ __device__ int team_svd_onesided(const Team& tm, R* A, int lda, int m, int n, R*
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
         R c, s;
-        if (active && jacobi_rot(al, be, ga, c, s)) {
+        if (active && jacobi_rot(al, be, ga, tol, c, s)) {
           if (gl == 0) *flag = 1;
           for (int r = gl; r < m; r += g) {
             const R ap = ap_[r], aq = aq_[r];

@@ -128,3 +128,21 @@ def test_rotated_d9_full_size_sampled(td):
     out, _ = _run(td, dem, det, chi=8, chi_mps=8)
     m, _ = _close(out, ref, 1e-6)
     assert m < 1e-6, m
+
+
+@pytest.mark.parametrize("case", ["rotated_d3", "point_d3", "repetition"])
+def test_fp32_storage_exact_regime(td, case):
+    """FP32 storage (FP64-accumulated Gram, FP32 update, FP64 truncation cores) where no
+    truncation happens: the result is the exact contraction up to the rounding of the
+    stored tensors, so it must match the exact transfer matrix to a few 1e-6 in log p."""
+    if case == "rotated_d3":
+        dem, B, seed, kw = rotated_phenomenological(3, 2, 0.05, 0.04), 64, 77, dict(chi=16, chi_mps=32)
+    elif case == "point_d3":
+        dem, B, seed, kw = point_sector_3d(3, 0.05), 64, 1000, dict(chi=8, chi_mps=64)
+    else:
+        dem, B, seed, kw = repetition_phenomenological(6, 4, 0.06, 0.03), 50, 5, dict(chi=32, chi_mps=8)
+    det, _ = sample_shots(dem, B, seed=seed)
+    ref = exact.transfer_matrix(dem, det)
+    out, _ = _run(td, dem, det, precision=td.TD_FP32, **kw)
+    m, _ = _close(out, ref, 5e-5)
+    assert m < 5e-5, m
