@@ -12,6 +12,7 @@
 
 #include "sweep.cuh"
 #include "td_internal.h"
+#include "team.cuh"
 
 namespace {
 thread_local std::string g_err;
@@ -132,8 +133,17 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   const int64_t cmx = std::max(cm, 2);
   const int64_t mps_stride = ((int64_t)cm * Dm * cmx + 3) / 4 * 4;
   const int64_t mF = 2LL * Dm * Dm * Dm * Dm;
-  const int64_t mW = std::max<int64_t>((int64_t)cm * Dm * 2 * Dm * cmx, (int64_t)cm * Dm * (cm * Dm + 1));
-  const int64_t mMT = (int64_t)cm * Dm * (cmx * Dm * 2 + 1);
+  // M^T (n x m) and V (m x m) with the bank-spreading leading dimensions of k_final
+  int64_t mMT = 0, mV = 0;
+  {
+    const int n_max = (int)(cmx * Dm * 2), m_max = cm * Dm;
+    for (int m = 1; m <= m_max; ++m) {
+      const int g = td::team_svd_group(256, n_max, m);
+      mMT = std::max<int64_t>(mMT, (int64_t)m * td::bank_ld32(n_max, g));
+      mV = std::max<int64_t>(mV, (int64_t)m * td::bank_ld32(m, g));
+    }
+  }
+  const int64_t mW = std::max<int64_t>((int64_t)cm * Dm * 2 * Dm * cmx, mV);
   const int64_t mC = (int64_t)cm * cmx * Dm * 2;
   const int64_t mS = 2LL * cm * Dm;
   const int64_t mOrd = ((int64_t)cm * Dm * 4 + net->elem - 1) / net->elem;

@@ -115,26 +115,29 @@ __global__ void k_final(FinalArgs fa) {
       const int aL = mdim[cur][x][0], aD = mdim[cur][x][1], aR = mdim[cur][x][2];
       const R* C = Cb[cc];
       (void)cA;
-      // T1[j][l][p][d][bb] = sum_a C[j][a][l][p] A[a][d][bb]
+      // T1[l][p][d][bb][j] = sum_a C[j][a][l][p] A[a][d][bb]  (j fastest: the lanes of one
+      // warp below read four j values of the same (l, p, d, bb) from distinct banks)
       R* T1 = W;
       const int n1 = cJ * L * 2 * aD * aR;
       for (int w = tm.tid; w < n1; w += tm.nt) {
         int e = w;
+        const int j = e % cJ; e /= cJ;
         const int bb = e % aR; e /= aR;
         const int d = e % aD; e /= aD;
         const int p = e % 2; e /= 2;
-        const int l = e % L; e /= L;
-        const int j = e;
+        const int l = e;
         R acc = R(0);
         for (int a = 0; a < aL; ++a) acc += C[((j * aL + a) * cL + l) * 2 + p] * A[(a * aD + d) * aR + bb];
         T1[w] = acc;
       }
       tm.sync();
-      // MT[(bb, r, q)][(j, u)] = sum_{l,p,d} T1[j][l][p][d][bb] F[p^q][l][r][d][u], stored
-      // column-major: column (j, u) of MT is row (j, u) of M (ld ldm, odd)
+      // MT[(bb, r, q)][(j, u)] = sum_{l,p,d} T1[l][p][d][bb][j] F[p^q][l][r][d][u], stored
+      // column-major: column (j, u) of MT is row (j, u) of M; leading dimensions chosen so
+      // the Jacobi lane groups of consecutive columns fall on disjoint banks
       const int nF = L * Rr * aD * U;
       const int m = cJ * U, n = aR * Rr * 2;
-      const int ldm = odd_ld(n), ldv = odd_ld(m);
+      const int ldm = bank_ld32(n, team_svd_group(tm.nt, n, m));
+      const int ldv = bank_ld32(m, team_svd_group(tm.nt, n, m));
       for (int w = tm.tid; w < m * n; w += tm.nt) {
         const int c = w / m, ju = w % m;      // consecutive lanes: consecutive u (F) and ju (MT)
         const int q = c % 2, r = (c / 2) % Rr, bb = c / (2 * Rr);
@@ -142,9 +145,9 @@ __global__ void k_final(FinalArgs fa) {
         R acc = R(0);
         for (int l = 0; l < L; ++l)
           for (int p = 0; p < 2; ++p) {
-            const R* t1 = T1 + (((j * L + l) * 2 + p) * aD) * aR + bb;
+            const R* t1 = T1 + (((l * 2 + p) * aD) * aR + bb) * cJ + j;
             const R* f = F + (p ^ q) * nF + ((l * Rr + r) * aD) * U + u;
-            for (int d = 0; d < aD; ++d) acc += t1[d * aR] * f[d * U];
+            for (int d = 0; d < aD; ++d) acc += t1[d * aR * cJ] * f[d * U];
           }
         MT[ju * ldm + c] = acc;
       }

@@ -353,6 +353,23 @@ __device__ void team_col_norms(const Team& tm, const R* A, int lda, int m, int n
 // Odd leading dimension >= rows (column-major storage without bank-aligned columns).
 __host__ __device__ __forceinline__ int odd_ld(int rows) { return rows | 1; }
 
+// Lanes per column pair used by team_svd_onesided for a team of nt threads and an m x n
+// matrix, and a leading dimension for 4-byte elements that puts the g-lane windows of
+// consecutive columns on disjoint shared-memory banks (ld = g mod 32).
+__host__ __device__ __forceinline__ int team_svd_group(int nt, int m, int n) {
+  const int half = (n + (n & 1)) / 2;
+  int g = half > 0 ? nt / half : 32;
+  if (g < 1) g = 1;
+  if (g > 32) g = 32;
+  int p2 = 1;
+  while (2 * p2 <= g) p2 *= 2;
+  g = p2;
+  const int rows_max = m > n ? m : n;
+  while (g > 1 && g > rows_max) g >>= 1;
+  return g;
+}
+__host__ __device__ __forceinline__ int bank_ld32(int rows, int g) { return (rows + 31) / 32 * 32 + (g & 31); }
+
 // Descending order of n non-negative values (ties: lower index first): order[rank] = j.
 // Ranks are counted on the bit patterns, which order non-negative IEEE values exactly.
 template <typename R>
