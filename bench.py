@@ -273,9 +273,19 @@ def main():
         tot32 = torch.logsumexp(lp32, dim=1)
         tot64 = torch.logsumexp(lp64, dim=1)
         dec_diff = int(((lp32[:, 1] > lp32[:, 0]) != (lp64[:, 1] > lp64[:, 0])).sum())
+        dflat = d.max(dim=1).values
+        # decisions compared only where the FP64 margin exceeds the mixed path's typical error
+        margin64 = (lp64[:, 1] - lp64[:, 0]).abs()
+        sure = margin64 > 1e-3
+        dec_diff_sure = int((((lp32[:, 1] > lp32[:, 0]) != (lp64[:, 1] > lp64[:, 0])) & sure).sum())
         fp64 = {"value": SHOTS / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64,
                 "max_dlogp_coset": float(d.max()), "median_dlogp_coset": float(d.median()),
-                "max_dlogP_total": float((tot32 - tot64).abs().max()), "decisions_differ": dec_diff}
+                "p99_dlogp_coset": float(torch.quantile(dflat, 0.99)),
+                "frac_shots_within_1e-3": float((dflat <= 1e-3).double().mean()),
+                "max_dlogP_total": float(torch.where(torch.isinf(tot32) & torch.isinf(tot64),
+                                                     torch.zeros_like(tot32), (tot32 - tot64).abs()).max()),
+                "decisions_differ": dec_diff,
+                "decisions_differ_where_margin_gt_1e-3": dec_diff_sure}
         net64.close()
 
     # roofline of the dominant kernel (largest summed device time in the timed region)
