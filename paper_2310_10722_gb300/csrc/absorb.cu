@@ -214,6 +214,118 @@ __global__ void __launch_bounds__(256) k_gram(SweepArgs a, const GateDesc* __res
   }
 }
 
+// Gram pass for bond dimensions <= 8 using the symmetry of G+ and G-.  Two lanes per row;
+// lane sub of a row holds the row with its halves swapped when sub = 1 (column q of the
+// lane's copy is column q ^ 4*sub of the row), assembled by shuffles.  Both lanes accumulate
+// the same fixed list of 20 entries (i, j) of their copy; lane sub's entry (i, j) is entry
+// (i ^ 4 sub, j ^ 4 sub) of the Gram.  The list holds one entry of each orbit of the 36
+// entries i <= j under i -> i ^ 4 (the four self-paired entries (i, i ^ 4) are computed by
+// both lanes, with identical results): 20 products per row and Gram instead of 32.
+namespace {
+__device__ constexpr int kSymI[20] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3};
+__device__ constexpr int kSymJ[20] = {0, 1, 2, 3, 4, 5, 6, 7, 1, 2, 3, 5, 6, 7, 2, 3, 6, 7, 3, 7};
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram_sym8(SweepArgs a, const GateDesc* __restrict__ gates,
+                                                   double* __restrict__ gram, int64_t n_jobs, int nchunk,
+                                                   int chunk_rows) {
+  constexpr int LPR = 2, BPL = 4, RPW = 16, NE = 20;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int64_t job = (int64_t)blockIdx.x * wpb + warp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int chi = a.chi;
+  double* lamv = reinterpret_cast<double*>(smem_raw) + (size_t)warp * kMaxBonds * chi;
+  if (job >= n_jobs) return;
+  const Job jb = decode_job(job, nchunk, a.B);
+  const GateDesc& gd = gates[jb.gi];
+  const SideDesc sd = gd.side[jb.side];
+  const int D = gd.D;
+  const double* lamb = a.lam + (int64_t)jb.b * a.nbonds * chi;
+  for (int w = lane; w < kMaxBonds * chi; w += 32) {
+    const int k = w / chi;
+    lamv[w] = (k < sd.nb) ? lamb[sd.bond[k] * chi + (w % chi)] : 1.0;
+  }
+  __syncwarp();
+  const Pairs pg = side_pairs(sd.P, sd.mask);
+  const int OI = sd.outer * sd.inner;
+  const int rows = pg.npairs * OI;
+  const int r_begin = jb.ch * chunk_rows;
+  const int r_end = min(rows, r_begin + chunk_rows);
+  const int64_t SZ = (int64_t)OI * D;
+  const T* gin = reinterpret_cast<const T*>(a.gamma) + (int64_t)jb.b * a.shot_elems + sd.in_off;
+  const int slot = lane / LPR, sub = lane % LPR, row0 = slot * LPR;
+  double accp[NE], accm[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    accp[e] = 0.0;
+    accm[e] = 0.0;
+  }
+  for (int r0 = r_begin; r0 < r_end; r0 += RPW) {
+    const int r = r0 + slot;
+    const bool live = r < r_end;
+    double yo[BPL], zo[BPL];
+    {
+      int pr = 0, o = 0, i = 0;
+      double w = 0.0;
+      if (live) {
+        pr = r / OI;
+        const int oi = r % OI;
+        o = oi / sd.inner;
+        i = oi % sd.inner;
+        w = row_weight<double>(sd, o, i, lamv, chi);
+      }
+      const T* plo = gin + pg.lo(pr) * SZ + (int64_t)o * D * sd.inner + i;
+      const T* phi = gin + pg.hi(pr) * SZ + (int64_t)o * D * sd.inner + i;
+#pragma unroll
+      for (int k = 0; k < BPL; ++k) {
+        const int q = sub * BPL + k;
+        double lo = 0.0, hi = 0.0;
+        if (live && q < D) {
+          lo = double(plo[(int64_t)q * sd.inner]);
+          hi = double(phi[(int64_t)q * sd.inner]);
+        }
+        yo[k] = (lo + hi) * w;
+        zo[k] = (lo - hi) * w;
+      }
+    }
+    double y[8], z[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int src = row0 + ((q / BPL) ^ sub);
+      y[q] = __shfl_sync(0xffffffffu, yo[q % BPL], src);
+      z[q] = __shfl_sync(0xffffffffu, zo[q % BPL], src);
+    }
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      accp[e] += y[kSymI[e]] * y[kSymJ[e]];
+      accm[e] += z[kSymI[e]] * z[kSymJ[e]];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < NE; ++e)
+#pragma unroll
+    for (int o = 16; o >= LPR; o >>= 1) {
+      accp[e] += __shfl_xor_sync(0xffffffffu, accp[e], o);
+      accm[e] += __shfl_xor_sync(0xffffffffu, accm[e], o);
+    }
+  if (slot == 0) {
+    double* out = gram + (jb.gb * nchunk + jb.ch) * 4 * chi * chi + (int64_t)(2 * jb.side) * chi * chi;
+    const int sw = 4 * sub;
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      const int i = kSymI[e] ^ sw, j = kSymJ[e] ^ sw;
+      if (i < D && j < D) {
+        out[i * D + j] = accp[e];
+        out[j * D + i] = accp[e];
+        out[chi * chi + i * D + j] = accm[e];
+        out[chi * chi + j * D + i] = accm[e];
+      }
+    }
+  }
+}
+
 // Update pass: Gamma_new[lo] = Y T+ + Z T-, Gamma_new[hi] = Y T+ - Z T-, in FP64 arithmetic
 // for both storage types (T), the result rounded to the storage type.
 template <typename T, int DMAX>
@@ -314,9 +426,15 @@ static cudaError_t gram_launch(const SweepArgs& a, const GateDesc* g, int count,
   const int64_t n_jobs = (int64_t)count * a.B * 2 * nchunk;
   const unsigned blocks = (unsigned)((n_jobs + wpb - 1) / wpb);
   const size_t smem = (size_t)wpb * kMaxBonds * a.chi * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_gram<T, DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_gram<T, DMAX><<<blocks, wpb * 32, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
+  if constexpr (DMAX == 8) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_sym8<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_sym8<T><<<blocks, wpb * 32, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_gram<T, DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram<T, DMAX><<<blocks, wpb * 32, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
+  }
   return cudaGetLastError();
 }
 
