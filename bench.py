@@ -172,6 +172,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU path")
     ap.add_argument("--shots", type=int, default=SHOTS, help="shots per GPU (profiling runs use fewer)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (reported beside the line)")
     args = ap.parse_args()
     SHOTS = args.shots
     rank = int(os.environ.get("RANK", "0"))
@@ -288,6 +289,37 @@ def main():
                 "decisions_differ_where_margin_gt_1e-3": dec_diff_sure}
         net64.close()
 
+    # other workloads of the same path, reported beside the headline (a few seconds each)
+    extra = None
+    if not args.no_extra and rank == 0:
+        from td_inputs import point_sector_3d
+        extra = {}
+
+        def rate(dem_x, shots, seed, **kw):
+            dx, _ = sample_shots(dem_x, shots, seed=seed)
+            dd = torch.from_numpy(dx).cuda()
+            nx = td.Network.from_dem(dem_x, mem_budget=32 << 30, **kw)
+            nx.coset_logprob(dd[: min(64, shots)])
+            torch.cuda.synchronize()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            lp = nx.coset_logprob(dd)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            ms_x = ea.elapsed_time(eb)
+            nx.close()
+            return shots / (ms_x / 1000.0), lp
+
+        r1, _ = rate(point_sector_3d(3, 0.05), 512, 1000, chi=8, chi_mps=64, precision=td.TD_FP64)
+        extra["point_sector_d3_p0.05_512shots_exact_fp64"] = {"value": r1, "unit": UNIT}
+        r32, lp32x = rate(dem, 256, SEED, chi=16, chi_mps=8, precision=td.TD_FP32)
+        r64, lp64x = rate(dem, 256, SEED, chi=16, chi_mps=8, precision=td.TD_FP64)
+        dx = (lp32x - lp64x).abs()
+        dx = torch.where(torch.isinf(lp32x) & torch.isinf(lp64x), torch.zeros_like(dx), dx)
+        extra["rotated_d9_chi16_chimps8_256shots"] = {
+            "mixed": {"value": r32, "unit": UNIT}, "fp64": {"value": r64, "unit": UNIT},
+            "max_dlogp_coset_mixed_vs_fp64": float(dx.max()), "median_dlogp_coset": float(dx.median())}
+
     # roofline of the dominant kernel (largest summed device time in the timed region)
     peaks = {}
     try:
@@ -340,6 +372,7 @@ def main():
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": int(info["launches_per_wave"] * waves * args.steps),
+        "other_workloads": extra,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
