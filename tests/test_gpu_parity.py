@@ -146,3 +146,15 @@ def test_fp32_storage_exact_regime(td, case):
     out, _ = _run(td, dem, det, precision=td.TD_FP32, **kw)
     m, _ = _close(out, ref, 5e-5)
     assert m < 5e-5, m
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-6), (1, 1e-3)])
+def test_point_sector_d5_truncated(td, precision, tol):
+    """3D point sector d=5 (25 sites, 4 check layers) at p=0.1 with truncation, against the
+    same-chi oracle: the code sizes of the uneven point-sector batch go through this path."""
+    dem = point_sector_3d(5, 0.1)
+    det, _ = sample_shots(dem, 6, seed=4)
+    ref = su.su_logprob(dem, det, chi=8, chi_mps=8)
+    out, _ = _run(td, dem, det, chi=8, chi_mps=8, precision=precision)
+    m, _ = _close(out, ref, tol)
+    assert m < tol, m
