@@ -320,6 +320,44 @@ def main():
             "mixed": {"value": r32, "unit": UNIT}, "fp64": {"value": r64, "unit": UNIT},
             "max_dlogp_coset_mixed_vs_fp64": float(dx.max()), "median_dlogp_coset": float(dx.median())}
 
+    # uneven batch: point-sector codes d = 5, 7, 9, 11 decoded together, their decode calls
+    # captured once in a CUDA graph and replayed (one network per code size)
+    if extra is not None:
+        from td_inputs import point_sector_3d
+        per, chi_u = 32, 16
+        nets_u, dets_u, outs_u = [], [], []
+        for dcode in (5, 7, 9, 11):
+            dem_u = point_sector_3d(dcode, 0.1)
+            du, _ = sample_shots(dem_u, per, seed=4000 + dcode)
+            nets_u.append(td.Network.from_dem(dem_u, chi=chi_u, chi_mps=8, precision=td.TD_FP32,
+                                              mem_budget=16 << 30))
+            dets_u.append(torch.from_numpy(du).cuda())
+            outs_u.append(torch.empty((per, 2), dtype=torch.float64, device="cuda"))
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):                  # warm-up outside the capture
+            for n_u, d_u, o_u in zip(nets_u, dets_u, outs_u):
+                n_u.coset_logprob(d_u, out=o_u)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        ref_u = [o.clone() for o in outs_u]
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for n_u, d_u, o_u in zip(nets_u, dets_u, outs_u):
+                n_u.coset_logprob(d_u, out=o_u)
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record(stream)
+        graph.replay()
+        gb.record(stream)
+        torch.cuda.synchronize()
+        extra["point_sector_uneven_d5_7_9_11_chi16_graph"] = {
+            "value": 4 * per / (ga.elapsed_time(gb) / 1000.0), "unit": UNIT, "shots": 4 * per,
+            "replay_matches_eager": all(torch.equal(a, b) for a, b in zip(ref_u, outs_u)),
+            "note": "p=0.1, chi=16, chi_mps=8, FP32 storage; one network per code size, all decode "
+                    "calls captured in one CUDA graph"}
+        for n_u in nets_u:
+            n_u.close()
+
     # roofline of the dominant kernel (largest summed device time in the timed region)
     peaks = {}
     try:
