@@ -305,7 +305,7 @@ cudaError_t launch_final(const FinalArgs& f, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_final<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_final<R><<<f.B, 256, smem, st>>>(f);
+  k_final<R><<<f.B, f.threads, smem, st>>>(f);
   return cudaGetLastError();
 }
 

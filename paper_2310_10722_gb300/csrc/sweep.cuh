@@ -36,6 +36,7 @@ struct FinalArgs {
   int64_t work_elems;        // work region size (elements)
   int64_t w_F, w_W, w_MT, w_C0, w_C1, w_s, w_ord;   // offsets inside the work region
   int32_t use_smem;          // work region in dynamic shared memory
+  int32_t threads;           // threads per block (one block per shot)
   int32_t nbonds, chi, nslots, slot;
   int32_t nx, ny, chi_mps;
   int32_t B;
