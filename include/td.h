@@ -53,9 +53,11 @@ typedef enum {
 
 typedef enum {
   TD_FP64 = 0,   /* FP64 storage and arithmetic everywhere (the plain FP64 GPU path) */
-  TD_FP32 = 1,   /* FP32 storage and contractions; FP64 truncation cores and log-sum */
-  TD_TF32 = 2    /* FP32 storage, layer contractions on tcgen05 (TF32 in, FP32 accumulate);
-                    FP64 truncation cores and log-sum */
+  TD_FP32 = 1,   /* FP32 storage of the site tensors; the sweep (Gram, update, site operators,
+                    truncation cores) computes in FP64 from it, the final boundary-MPS
+                    contraction in FP32, the log-sum in FP64 */
+  TD_TF32 = 2    /* reserved: tensor-core contractions with FP32 accumulation; rejected by
+                    td_build_network with TD_ERR_UNSUPPORTED */
 } td_precision;
 
 /* DEM triple (H, p, l) of Sec. 2.4, host memory, CSR by rows. */
