@@ -84,6 +84,23 @@ def cpu_baseline(chi, n_shots=CPU_SAMPLE, first=0):
                       f"{len(jobs)} spawned processes, wall {wall:.2f} s (CPU {sum(r[0] for r in res):.1f} s)"}
 
 
+# ---------------------------------------------------------------- replicas
+def replica_first_shot(rank, shots_per_rank):
+    """First shot of a rank's slice of the seeded stream: ranks decode disjoint, contiguous
+    slices, so N replicas together decode the first N * shots_per_rank shots."""
+    return rank * shots_per_rank
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """Largest value over the ranks (the timed region is the slowest replica's)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -202,7 +219,7 @@ def main():
 
     chi = args.chi
     dem = rotated_phenomenological(D_CODE, ROUNDS, P_DATA, Q_MEAS)
-    det_np, _ = sample_shots(dem, SHOTS, seed=SEED, first_shot=rank * SHOTS)
+    det_np, _ = sample_shots(dem, SHOTS, seed=SEED, first_shot=replica_first_shot(rank, SHOTS))
     det = torch.from_numpy(det_np).cuda()
     net = td.Network.from_dem(dem, chi=chi, chi_mps=chi, precision=td.TD_FP32, mem_budget=96 << 30,
                               max_wave=SHOTS)
@@ -232,10 +249,7 @@ def main():
     prof = net.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1000.0
-    t_local = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max = float(t_local.item())
+    t_max = max_over_ranks(dev_s, world, device="cuda")
     value = world * SHOTS * args.steps / t_max
 
     # end to end through the host-buffer entry point (pinned copies inside the timed region)
