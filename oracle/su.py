@@ -423,3 +423,33 @@ def plan_det(plan, s, t):
             d[(ss, tt)] = i
         plan._det_at = d
     return plan._det_at[(s, t)]
+
+
+def su_grad_total_logprob(dem, det_bits: np.ndarray, chi: int, chi_mps: int, cutoff: float = 1e-12,
+                          mrtol: float = 1e-8):
+    """(log P [B], d log P / d p [B, n_mech]) of the truncated sweep, P(m) = sum_L p_{m,L}.
+
+    The contraction of Sec. 2.4 / Sec. 3.4 is affine in every rate p_j (mechanism j is one
+    weighted node): P = (1 - p_j) P_{x_j=0} + p_j P_{x_j=1}, so
+        d log P / d p_j = (P_{x_j=1} - P_{x_j=0}) / P,
+    with P_{x_j=b} the network with mechanism j forced to b (rate set to b).  Each of the
+    three values is the truncated sweep of this module at the same chi; without truncation
+    this is the exact gradient of exact.grad_total_logprob.  Mechanisms without detectors
+    only mix the classes and get 0.
+    """
+    def total(d):
+        lp = su_logprob(d, det_bits, chi, chi_mps, cutoff, mrtol)
+        with np.errstate(invalid="ignore"):
+            return np.logaddexp(lp[:, 0], lp[:, 1])
+    base = total(dem)
+    grad = np.zeros((det_bits.shape[0], dem.n_mech))
+    p0 = np.array(dem.p, dtype=np.float64)
+    for j in range(dem.n_mech):
+        pj = p0.copy()
+        pj[j] = 1.0
+        l1 = total(dem.with_rates(pj))
+        pj[j] = 0.0
+        l0 = total(dem.with_rates(pj))
+        with np.errstate(invalid="ignore"):
+            grad[:, j] = np.exp(l1 - base) - np.exp(l0 - base)
+    return base, grad
