@@ -153,11 +153,30 @@ td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_
 td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
                                   void* stream);
 
-/* Gradient of the mean total log-probability (1/B) sum_b log P(m_b), P(m) = sum_L p_{m,L},
- * with respect to every mechanism rate (the adjoint of the Sec. 4 sweep).  p_dev: device
- * double [n_mech] rates to use (NULL: the build rates); logP_dev: device double [B];
- * grad_dev: device double [n_mech].  Not implemented in this build: returns
- * TD_ERR_UNSUPPORTED. */
+/* Gradient of the mean total log-probability (1/B) sum_b log P(m_b), P(m) = sum_L p_{m,L}
+ * (Sec. 2.4), with respect to every mechanism rate; the paper has no gradient.
+ *
+ * P(m) is affine in each rate p_j (mechanism j is one weighted node of the network of
+ * Sec. 3.4), so d log P / d p_j = (P_{x_j=1} - P_{x_j=0}) / P, where P_{x_j=x} is the
+ * network with p_j set to x.  All three values are computed by this library's decoder (the
+ * Sec. 4 sweep at the network's chi, chi_mps and precision): the call decodes every shot
+ * once as is and twice per mechanism whose rate enters the network (each forced copy
+ * replaces one parameter object: a site-local matrix, a gate's p or a readout), batched
+ * as B * (1 + 2 n_forced) virtual shots in the network's waves.  Without truncation the
+ * result is the exact gradient; with truncation each P is the decoder's estimate.
+ * Mechanisms without detectors only mix the classes and get 0; a shot whose P comes out
+ * 0 contributes nothing (the mean still divides by B).
+ *
+ * det_dev: device uint8 [B][n_det]; p_dev: device double [n_mech] rates in [0, 1], or
+ * NULL for the network's current rates.  A p_dev different from the current rates must
+ * keep the network's structure (TD_ERR_INVALID otherwise) and becomes the network's rates
+ * for this and later calls.  logP_dev: device double [B] (log P of each shot at the
+ * rates); grad_dev: device double [n_mech].
+ * The host builds the forced parameter objects (2 n_mech plans, cached while the rates do
+ * not change) and synchronises `stream` before it does; the decodes and the reduction are
+ * then queued on `stream` and the call returns without waiting for them.  Errors:
+ * TD_ERR_INVALID (null buffers, rates outside [0, 1], B * (1 + 2 n_forced) >= 2^31),
+ * TD_ERR_OOM, TD_ERR_CUDA. */
 td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev,
                           double* logP_dev, double* grad_dev, void* stream);
 

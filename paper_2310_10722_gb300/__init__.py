@@ -125,11 +125,18 @@ class Network:
         return out
 
     def grad_logprob(self, det, p=None, stream=None):
+        """(log P [B], d mean_b log P / d p [n_mech]) with P(m) = sum_L p_{m,L}, on det's
+        device.  p: float64 rates on the device (None: the current rates); a given p
+        becomes the network's rates for later calls too."""
         import torch
         self._check_det(det)
         B = det.shape[0]
         logP = torch.empty(B, dtype=torch.float64, device=det.device)
         grad = torch.empty(self.n_mech, dtype=torch.float64, device=det.device)
+        if p is not None:
+            if p.dtype != torch.float64 or p.device != det.device or p.numel() != self.n_mech:
+                raise ValueError("p must be float64 [n_mech] on the detector buffer's device")
+            p = p.contiguous()
         pp = C.c_void_p(p.data_ptr()) if p is not None else None
         check(self._lib.td_grad_logprob(self._h, C.c_void_p(det.data_ptr()), B, pp, C.c_void_p(logP.data_ptr()),
                                         C.c_void_p(grad.data_ptr()), self._stream(stream)))
@@ -174,3 +181,24 @@ class Network:
             self.close()
         except Exception:
             pass
+
+
+def mean_logprob(net: "Network", det, p):
+    """(1/B) sum_b log P(m_b) as a differentiable function of the rates p (float64
+    [n_mech] on det's device): the value and its gradient come from one td_grad_logprob
+    call, so torch.autograd can drive a maximum-likelihood fit of the noise model."""
+    import torch
+
+    class _MeanLogProb(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, rates):
+            logP, grad = net.grad_logprob(det, rates.detach())
+            ctx.save_for_backward(grad)
+            return logP.mean()
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return g * grad
+
+    return _MeanLogProb.apply(p)

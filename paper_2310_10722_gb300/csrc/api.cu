@@ -49,6 +49,53 @@ struct td_network {
   size_t bytes = 0;
   int64_t launches_per_wave = 0;
   std::vector<void*> allocs;
+  // copy of the problem (the gradient pass rebuilds the parameter objects at other rates)
+  std::vector<int32_t> H_indptr, H_indices, L_indptr, L_indices, det_xyt;
+  std::vector<double> rates;
+  int32_t n_obs = 0;
+  td_options opt{};
+  // gradient pass: override table for the current rates, per-mechanism entries (0: none)
+  std::vector<double> ovr_rates;
+  std::vector<td::Override> ovr_host;
+  std::vector<int32_t> ovr_of;           // [n_mech][2] override index at p_j = 0, 1
+  td::Override* d_ovr = nullptr;
+  size_t d_ovr_cap = 0;
+  td::VShot* d_vs = nullptr;
+  size_t d_vs_cap = 0;
+  double* d_vlogp = nullptr;
+  size_t d_vlogp_cap = 0;
+  int32_t* d_act = nullptr;
+  size_t d_act_cap = 0;
+  td_dem dem_view(const double* p) const {
+    td_dem d{};
+    d.n_det = plan.n_det; d.n_mech = plan.n_mech; d.n_obs = n_obs;
+    d.H_indptr = H_indptr.data(); d.H_indices = H_indices.data();
+    d.L_indptr = L_indptr.data(); d.L_indices = L_indices.data();
+    d.p = p;
+    return d;
+  }
+  td_layout layout_view() const {
+    td_layout l{};
+    l.det_xyt = det_xyt.data();
+    return l;
+  }
+  // growable device buffer (freed with the network)
+  template <typename P>
+  bool reserve(P*& ptr, size_t& cap, size_t n) {
+    if (n <= cap && ptr) return true;
+    if (ptr) {
+      cudaFree(ptr);
+      allocs.erase(std::remove(allocs.begin(), allocs.end(), (void*)ptr), allocs.end());
+      ptr = nullptr;
+      cap = 0;
+    }
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(P)) != cudaSuccess) { cudaGetLastError(); return false; }
+    allocs.push_back(q);
+    ptr = reinterpret_cast<P*>(q);
+    cap = n;
+    return true;
+  }
   // kernel timing (td_network_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -121,6 +168,14 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   if (st != TD_OK) { delete net; return fail(st, err); }
   td::Plan& P = net->plan;
   if (P.nx > 32) { delete net; return fail(TD_ERR_UNSUPPORTED, "grid wider than 32 sites"); }
+  net->H_indptr.assign(dem->H_indptr, dem->H_indptr + dem->n_det + 1);
+  net->H_indices.assign(dem->H_indices, dem->H_indices + dem->H_indptr[dem->n_det]);
+  net->L_indptr.assign(dem->L_indptr, dem->L_indptr + dem->n_obs + 1);
+  net->L_indices.assign(dem->L_indices, dem->L_indices + dem->L_indptr[dem->n_obs]);
+  net->det_xyt.assign(layout->det_xyt, layout->det_xyt + 3 * (size_t)dem->n_det);
+  net->rates.assign(dem->p, dem->p + dem->n_mech);
+  net->n_obs = dem->n_obs;
+  net->opt = o;
   const int chi = P.chi, cm = P.chi_mps, Dm = P.max_final_D;
   if ((int64_t)cm * Dm > 256) { delete net; return fail(TD_ERR_UNSUPPORTED, "chi_mps * final bond dimension must be <= 256"); }
   if (o.precision == TD_TF32) { delete net; return fail(TD_ERR_UNSUPPORTED, "TF32 tensor-core path not built yet"); }
@@ -212,6 +267,8 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
     delete net;
     return cuda_fail(e, "descriptor upload");
   }
+  // pageable uploads may still be in flight when cudaMemcpy returns
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) { delete net; return cuda_fail(e, "descriptor upload"); }
   int64_t launches = 1 + 2;   // init, final, finalize
   const int per_round = 3;   // Gram, core, update
   for (const td::LayerPlan& L : P.layers) launches += 1 + per_round * (int64_t)L.rounds.size();
@@ -230,7 +287,8 @@ struct NetProf : td::Prof {
 };
 
 static td_status run(td_network* net, const uint8_t* det, int64_t B, double* logp, int32_t* decision, double* margin,
-                     cudaStream_t st, void* final_scratch = nullptr) {
+                     cudaStream_t st, void* final_scratch = nullptr, const td::VShot* vs = nullptr,
+                     const td::Override* ovr = nullptr) {
   td::Plan& P = net->plan;
   NetProf prof(net, st);
   for (int64_t w0 = 0; w0 < B; w0 += net->wave) {
@@ -250,6 +308,8 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     a.gram_cutoff = P.gram_cutoff;
     a.svd_cutoff = P.svd_cutoff;
     a.multiplet_rtol = P.multiplet_rtol;
+    a.vs = vs;
+    a.ovr = ovr;
     const bool f64 = P.precision == TD_FP64;
     cudaError_t e;
     {
@@ -260,6 +320,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     if (e != cudaSuccess) return cuda_fail(e, "init launch");
     for (int32_t t = 0; t < P.T; ++t) {
       const td::LayerPlan& L = P.layers[t];
+      a.layer = t;
       {
         td_network::Mark mk(net, TD_K_LOCAL, st);
         e = f64 ? td::launch_local<double, double>(a, net->d_locals + L.local_first, P.S, st)
@@ -291,6 +352,9 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     f.B = Bw;
     f.svd_cutoff = P.svd_cutoff;
     f.multiplet_rtol = P.multiplet_rtol;
+    f.vs = vs;
+    f.ovr = ovr;
+    f.wave_first = (int32_t)w0;
     {
       td_network::Mark mk(net, TD_K_FINAL, st);
       e = f64 ? td::launch_final<double, double>(f, st) : td::launch_final<float, float>(f, st);
@@ -309,6 +373,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     z.B = Bw;
     z.offset_all = P.offset_all;
     for (int i = 0; i < 4; ++i) z.mix[i] = P.glob_mix[i];
+    z.vs = vs;
     {
       td_network::Mark mk(net, TD_K_FINALIZE, st);
       e = td::launch_finalize(z, st);
@@ -387,12 +452,159 @@ td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64
   return run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream), scr);
 }
 
+// ---- gradient pass ----------------------------------------------------------------------
+// The parameter objects of a plan that depend on the rates: site-local K, gate p, readout R.
+static int differing_object(const td::Plan& A, const td::Plan& B, td::Override& o) {
+  int found = 0;
+  for (size_t i = 0; i < A.locals.size(); ++i)
+    if (std::memcmp(A.locals[i].K, B.locals[i].K, sizeof(A.locals[i].K)) != 0) {
+      o.kind = td::kOvrLocal;
+      o.target = (int32_t)i;   // layer * S + site (locals are emitted layer by layer)
+      std::memset(o.val, 0, sizeof(o.val));
+      std::memcpy(o.val, B.locals[i].K, sizeof(B.locals[i].K));
+      ++found;
+    }
+  for (size_t i = 0; i < A.gates.size(); ++i)
+    if (A.gates[i].p != B.gates[i].p) {
+      o.kind = td::kOvrGate;
+      o.target = (int32_t)i;
+      std::memset(o.val, 0, sizeof(o.val));
+      o.val[0] = B.gates[i].p;
+      ++found;
+    }
+  for (size_t i = 0; i < A.finals.size(); ++i)
+    if (std::memcmp(A.finals[i].R, B.finals[i].R, sizeof(A.finals[i].R)) != 0) {
+      o.kind = td::kOvrRead;
+      o.target = (int32_t)i;
+      std::memset(o.val, 0, sizeof(o.val));
+      std::memcpy(o.val, B.finals[i].R, sizeof(B.finals[i].R));
+      ++found;
+    }
+  return found;
+}
+
+static bool same_structure(const td::Plan& A, const td::Plan& B) {
+  return A.locals.size() == B.locals.size() && A.gates.size() == B.gates.size() &&
+         A.finals.size() == B.finals.size() && A.shot_elems == B.shot_elems && A.n_bonds == B.n_bonds;
+}
+
+// Sets the network's rates to `rates` (parameter objects rebuilt and uploaded) and builds
+// the override table of every mechanism forced to 0 and to 1.
+static td_status prepare_overrides(td_network* net, const std::vector<double>& rates, cudaStream_t st) {
+  if (!net->ovr_rates.empty() && net->ovr_rates == rates) return TD_OK;
+  std::string err;
+  td::Plan& P = net->plan;
+  const td_layout lay = net->layout_view();
+  if (rates != net->rates) {
+    td::Plan Q;
+    const td_dem d = net->dem_view(rates.data());
+    td_status s = td::build_plan(d, lay, net->opt, Q, err);
+    if (s != TD_OK) return fail(s, "rates: " + err);
+    if (!same_structure(P, Q)) return fail(TD_ERR_INVALID, "rates change the network's structure");
+    for (size_t i = 0; i < P.locals.size(); ++i) std::memcpy(P.locals[i].K, Q.locals[i].K, sizeof(P.locals[i].K));
+    for (size_t i = 0; i < P.gates.size(); ++i) P.gates[i].p = Q.gates[i].p;
+    for (size_t i = 0; i < P.finals.size(); ++i) std::memcpy(P.finals[i].R, Q.finals[i].R, sizeof(P.finals[i].R));
+    std::memcpy(P.glob_mix, Q.glob_mix, sizeof(P.glob_mix));
+    cudaError_t e;
+    if ((!P.gates.empty() && (e = cudaMemcpyAsync(net->d_gates, P.gates.data(), sizeof(td::GateDesc) * P.gates.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(net->d_locals, P.locals.data(), sizeof(td::LocalDesc) * P.locals.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(net->d_finals, P.finals.data(), sizeof(td::FinalSite) * P.finals.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cuda_fail(e, "descriptor upload");
+    net->rates = rates;
+  }
+  const int32_t n_mech = P.n_mech;
+  net->ovr_host.assign(1, td::Override{});
+  net->ovr_host[0].kind = td::kOvrNone;
+  net->ovr_of.assign(2 * (size_t)n_mech, 0);
+  std::vector<double> r = rates;
+  for (int32_t j = 0; j < n_mech; ++j) {
+    for (int x = 0; x < 2; ++x) {
+      r[j] = (double)x;
+      td::Plan Q;
+      const td_dem d = net->dem_view(r.data());
+      td_status s = td::build_plan(d, lay, net->opt, Q, err);
+      if (s != TD_OK) return fail(s, "forced rate: " + err);
+      if (!same_structure(P, Q)) return fail(TD_ERR_INVALID, "forcing a rate changes the network's structure");
+      td::Override o{};
+      const int nd = differing_object(P, Q, o);
+      if (nd > 1) return fail(TD_ERR_INVALID, "a mechanism rate enters more than one parameter object");
+      if (nd == 1) {
+        net->ovr_of[2 * (size_t)j + x] = (int32_t)net->ovr_host.size();
+        net->ovr_host.push_back(o);
+      }
+    }
+    r[j] = rates[j];
+  }
+  if (!net->reserve(net->d_ovr, net->d_ovr_cap, net->ovr_host.size())) return fail(TD_ERR_OOM, "override table");
+  cudaError_t e = cudaMemcpyAsync(net->d_ovr, net->ovr_host.data(), sizeof(td::Override) * net->ovr_host.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "override upload");
+  net->ovr_rates = rates;
+  return TD_OK;
+}
+
 td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev, double* logP_dev,
                           double* grad_dev, void* stream) {
   g_err.clear();
-  (void)det_dev; (void)B; (void)p_dev; (void)logP_dev; (void)grad_dev; (void)stream;
-  if (!net) return fail(TD_ERR_INVALID, "null network");
-  return fail(TD_ERR_UNSUPPORTED, "adjoint sweep not built yet");
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (!grad_dev || (B > 0 && !logP_dev)) return fail(TD_ERR_INVALID, "null output buffer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int32_t n_mech = net->plan.n_mech;
+  std::vector<double> rates = net->rates;
+  cudaError_t e;
+  if (p_dev) {
+    e = cudaMemcpyAsync(rates.data(), p_dev, sizeof(double) * n_mech, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "rate copy");
+    for (int32_t j = 0; j < n_mech; ++j)
+      if (!(rates[j] >= 0.0 && rates[j] <= 1.0)) return fail(TD_ERR_INVALID, "rate outside [0, 1]");
+  }
+  // the override table is built on the host; no kernel of an earlier call may still read it
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  s = prepare_overrides(net, rates, st);
+  if (s != TD_OK) return s;
+  // forced mechanisms, in order; virtual shots b * NV + (0 | 1 + 2a + x)
+  std::vector<int32_t> act(n_mech, -1);
+  std::vector<int32_t> forced;
+  for (int32_t j = 0; j < n_mech; ++j)
+    if (net->ovr_of[2 * (size_t)j] || net->ovr_of[2 * (size_t)j + 1]) {
+      act[j] = (int32_t)forced.size();
+      forced.push_back(j);
+    }
+  const int32_t NV = 1 + 2 * (int32_t)forced.size();
+  const int64_t Bv = B * NV;
+  if (Bv > ((int64_t)1 << 31) - 1) return fail(TD_ERR_INVALID, "B * (1 + 2 * forced mechanisms) exceeds 2^31 - 1");
+  if (!net->reserve(net->d_act, net->d_act_cap, (size_t)n_mech) ||
+      !net->reserve(net->d_vs, net->d_vs_cap, (size_t)Bv) ||
+      !net->reserve(net->d_vlogp, net->d_vlogp_cap, (size_t)Bv * 2))
+    return fail(TD_ERR_OOM, "gradient pass buffers");
+  std::vector<td::VShot> vs((size_t)Bv);
+  for (int64_t b = 0; b < B; ++b) {
+    td::VShot* v = &vs[(size_t)(b * NV)];
+    v[0].base = (int32_t)b;
+    v[0].ovr = 0;
+    for (size_t a = 0; a < forced.size(); ++a)
+      for (int x = 0; x < 2; ++x) {
+        v[1 + 2 * a + x].base = (int32_t)b;
+        v[1 + 2 * a + x].ovr = net->ovr_of[2 * (size_t)forced[a] + x];
+      }
+  }
+  // pageable sources: each asynchronous copy has staged its source when it returns
+  if (n_mech > 0 && (e = cudaMemcpyAsync(net->d_act, act.data(), sizeof(int32_t) * n_mech, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "gradient map upload");
+  if (Bv > 0 && (e = cudaMemcpyAsync(net->d_vs, vs.data(), sizeof(td::VShot) * (size_t)Bv, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "virtual shot upload");
+  if (Bv > 0) {
+    s = run(net, det_dev, Bv, net->d_vlogp, nullptr, nullptr, st, nullptr, net->d_vs, net->d_ovr);
+    if (s != TD_OK) return s;
+  }
+  e = td::launch_grad_combine(net->d_vlogp, B, NV, net->d_act, n_mech, logP_dev, grad_dev, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gradient combine launch");
+  return TD_OK;
 }
 
 td_status td_debug_sweep(td_network* net, const uint8_t* det_dev, int64_t B, int32_t n_gates, double* lam_dev,

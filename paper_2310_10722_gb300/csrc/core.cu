@@ -212,7 +212,8 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
     if (tm.tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] = -INFINITY;
     return;
   }
-  const double p = gd.p;
+  const Override* ov = vshot_ovr(a.vs, a.ovr, a.wave_first, b, kOvrGate, a.gate_base + gi);
+  const double p = ov ? ov->val[0] : gd.p;
   const double cpp = 0.5, cpm = 0.5 * (1.0 - 2.0 * p);
   for (int w = tm.tid; w < rA * D; w += tm.nt) {     // R_A Lambda, in place
     const int i = w / D, q = w % D;

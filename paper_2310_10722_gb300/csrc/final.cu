@@ -28,6 +28,8 @@ __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y
     return;
   }
   const FinalSite& fs = fa.sites[s];
+  const Override* ov = vshot_ovr(fa.vs, fa.ovr, fa.wave_first, b, kOvrRead, s);
+  const double* Rv = ov ? ov->val : fs.R;
   const double* lam = fa.lam + (int64_t)b * fa.nbonds * fa.chi;
   for (int w = tm.tid; w < 4 * fa.chi; w += tm.nt) {
     const int dir = w / fa.chi, i = w % fa.chi;
@@ -61,8 +63,8 @@ __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y
     R a0 = R(0), a1 = R(0);
     for (int ph = 0; ph < fs.P; ++ph) {
       const R gv = g[(int64_t)ph * rest + off];
-      a0 += R(fs.R[ph * 2 + 0]) * gv;
-      a1 += R(fs.R[ph * 2 + 1]) * gv;
+      a0 += R(Rv[ph * 2 + 0]) * gv;
+      a1 += R(Rv[ph * 2 + 1]) * gv;
     }
     F[w] = a0 * wgt;
     F[rest + w] = a1 * wgt;
@@ -279,7 +281,7 @@ __global__ void k_finalize(FinalizeArgs f) {
   double zz[2] = {f.mix[0] * z0 + f.mix[1] * z1, f.mix[2] * z0 + f.mix[3] * z1};
   int off = 0;
   if (f.offset_all) {
-    const uint8_t* m = f.det + (int64_t)(f.wave_first + b) * f.n_det;
+    const uint8_t* m = f.det + (int64_t)vshot_row(f.vs, f.wave_first, b) * f.n_det;
     for (int i = 0; i < f.n_det; ++i) off ^= m[i] & 1;
   }
   double lp[2];

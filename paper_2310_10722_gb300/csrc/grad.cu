@@ -1,0 +1,50 @@
+// Gradient of the mean total log-probability from the virtual shots of the gradient pass.
+//
+// P(m) = sum_L p_{m,L} is affine in every mechanism rate (Sec. 2.4: each mechanism is one
+// factor p^x (1-p)^(1-x) of the sum), so d log P / d p_j = (P_{x_j=1} - P_{x_j=0}) / P.
+// Virtual shot (b, 0) decodes shot b at the given rates; (b, 1 + 2a + x) decodes it with
+// the parameter object of the a-th mechanism forced to x.  All three are the decoder's
+// (truncated) values; without truncation the result is the exact gradient.
+#include <cmath>
+
+#include "sweep.cuh"
+
+namespace td {
+
+__device__ __forceinline__ double total_of(const double* lp) {
+  const double a = lp[0], c = lp[1];
+  const double m = fmax(a, c);
+  if (!(m > -INFINITY)) return -INFINITY;
+  return m + log(exp(a - m) + exp(c - m));
+}
+
+// One thread per mechanism (gradient) and per shot (log P); shots summed in order.
+__global__ void k_grad_combine(const double* __restrict__ vlogp, int64_t B, int32_t NV,
+                               const int32_t* __restrict__ act, int32_t n_mech, double* __restrict__ logP,
+                               double* __restrict__ grad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B) logP[i] = total_of(vlogp + i * NV * 2);
+  if (i >= n_mech) return;
+  const int a = act[i];
+  double acc = 0.0;
+  if (a >= 0)
+    for (int64_t b = 0; b < B; ++b) {
+      const double* v = vlogp + b * NV * 2;
+      const double t = total_of(v);
+      if (!(t > -INFINITY)) continue;   // a shot of probability 0 contributes nothing
+      const double t0 = total_of(v + 2 * (1 + 2 * a));
+      const double t1 = total_of(v + 2 * (2 + 2 * a));
+      acc += exp(t1 - t) - exp(t0 - t);
+    }
+  grad[i] = B > 0 ? acc / (double)B : 0.0;
+}
+
+cudaError_t launch_grad_combine(const double* vlogp, int64_t B, int32_t NV, const int32_t* act, int32_t n_mech,
+                                double* logP, double* grad, cudaStream_t st) {
+  const int64_t n = B > n_mech ? B : n_mech;
+  if (n == 0) return cudaSuccess;
+  k_grad_combine<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(vlogp, B, NV, act, n_mech, logP, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace td

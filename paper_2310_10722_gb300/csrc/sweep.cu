@@ -60,10 +60,12 @@ __global__ void k_local(SweepArgs a, const LocalDesc* __restrict__ locals) {
   const LocalDesc d = locals[s];
   __shared__ double K[kMaxPhys * kMaxPhys];
   __shared__ double red[32];
-  const int m = a.det[(int64_t)(a.wave_first + b) * a.n_det + d.det] & 1;
+  const int m = a.det[(int64_t)vshot_row(a.vs, a.wave_first, b) * a.n_det + d.det] & 1;
+  const Override* o = vshot_ovr(a.vs, a.ovr, a.wave_first, b, kOvrLocal, a.layer * (int)gridDim.x + s);
+  const double* Ksrc = o ? o->val : d.K;
   if (threadIdx.x < d.P * d.P) {
     const int row = threadIdx.x / d.P, col = threadIdx.x % d.P;
-    K[threadIdx.x] = d.K[(row ^ m) * d.P + col];     // rows of X^m K
+    K[threadIdx.x] = Ksrc[(row ^ m) * d.P + col];     // rows of X^m K
   }
   __syncthreads();
   T* g = reinterpret_cast<T*>(a.gamma) + (int64_t)b * a.shot_elems + d.off;
@@ -116,6 +118,7 @@ cudaError_t launch_round(const SweepArgs& a0, const GateDesc* gates, const Round
   const int D = std::max(rd.maxD, rd.maxDn);
   SweepArgs a = a0;
   a.gram_chunks = absorb_chunks(rd.max_rows, kChunkRows);
+  a.gate_base = rd.first;
   auto B = [&](int k) { if (prof) prof->begin(k); };
   auto E = [&](int k) { if (prof) prof->end(k); };
   B(TD_K_GRAM);

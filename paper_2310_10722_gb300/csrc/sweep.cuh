@@ -19,7 +19,23 @@ struct SweepArgs {
   int32_t B;                // shots in this wave
   int32_t gram_chunks;      // partial Grams per (gate, shot) of the current round (row chunks)
   double gram_cutoff, svd_cutoff, multiplet_rtol;
+  // gradient pass (null otherwise): virtual shots [*] and their override table
+  const VShot* vs;
+  const Override* ovr;
+  int32_t layer;            // current layer (local operators)
+  int32_t gate_base;        // global index of the round's first gate (core)
 };
+
+// Detector row and override of shot b of a wave (plain decode: row wave_first + b, none).
+__device__ __forceinline__ int vshot_row(const VShot* vs, int wave_first, int b) {
+  return vs ? vs[wave_first + b].base : wave_first + b;
+}
+__device__ __forceinline__ const Override* vshot_ovr(const VShot* vs, const Override* ovr, int wave_first, int b,
+                                                     int kind, int target) {
+  if (!vs) return nullptr;
+  const Override* o = ovr + vs[wave_first + b].ovr;
+  return (o->kind == kind && o->target == target) ? o : nullptr;
+}
 
 struct FinalArgs {
   const void* gamma;
@@ -41,6 +57,9 @@ struct FinalArgs {
   int32_t nx, ny, chi_mps;
   int32_t B;
   double svd_cutoff, multiplet_rtol;
+  const VShot* vs;           // gradient pass: virtual shots and overrides (null otherwise)
+  const Override* ovr;
+  int32_t wave_first;
 };
 
 struct FinalizeArgs {
@@ -52,6 +71,7 @@ struct FinalizeArgs {
   double* margin;            // [*] or null
   int32_t nslots, n_det, wave_first, B, offset_all;
   double mix[4];
+  const VShot* vs;           // gradient pass (null otherwise)
 };
 
 // Optional timing hooks around each kernel launch (kernel class ids of td_kernel_class).
@@ -71,6 +91,10 @@ cudaError_t launch_round(const SweepArgs& a, const GateDesc* gates, const Round&
 template <typename T, typename R>
 cudaError_t launch_final(const FinalArgs& f, cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st);
+// Gradient pass (grad.cu): log P per shot and d mean log P / d p_j from the virtual shots'
+// log p [B * NV][2]; act[j] = the mechanism's position among the forced ones, or -1.
+cudaError_t launch_grad_combine(const double* vlogp, int64_t B, int32_t NV, const int32_t* act, int32_t n_mech,
+                                double* logP, double* grad, cudaStream_t st);
 
 // Truncation core (core.cu): the simple-update core of every gate of a round; Dm = the
 // round's largest active bond dimension; gram: FP64 partial Grams.

@@ -68,6 +68,23 @@ struct FinalSite {
   double R[kMaxPhys * 2];
 };
 
+// Parameter override of the gradient pass.  The network is affine in every mechanism rate,
+// and the rate of one mechanism enters exactly one parameter object: a site-local matrix K
+// (single-detector mechanisms of layers < T-1, vertical mechanisms), a gate's p (two-
+// detector mechanisms of one layer) or a site's readout R (single-detector mechanisms of
+// the last layer).  A virtual shot decodes the detector bits of shot `base` with at most
+// one object replaced by its value at p_j = 0 or 1.
+enum { kOvrNone = 0, kOvrLocal = 1, kOvrGate = 2, kOvrRead = 3 };
+struct Override {
+  int32_t kind;
+  int32_t target;       // local: layer * S + site; gate: global gate index; readout: site
+  double val[kMaxPhys * kMaxPhys];   // K (P x P), p (val[0]) or R (P x 2), row major
+};
+struct VShot {
+  int32_t base;         // row of the detector buffer
+  int32_t ovr;          // index into the override table (entry 0: no override)
+};
+
 struct Round {             // gates on disjoint bonds, run as one batch
   int32_t first, count;    // range in the gate descriptor array
   int32_t maxD, maxDn;
