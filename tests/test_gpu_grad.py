@@ -62,7 +62,7 @@ def test_grad_untruncated_repetition_merged_duplicates(td):
     dem = DEM(base.n_det, base.n_obs, list(base.mech_dets) * 2, list(base.mech_obs) * 2,
               np.concatenate([base.p, 0.5 * base.p]), base.det_xyt.copy(), "rep-dup", {})
     det, _ = sample_shots(base, 12, seed=23)
-    logP, g, _ = _grad(td, dem, det, chi=32, chi_mps=32)
+    logP, g, _ = _grad(td, dem, det, chi=32, chi_mps=8)
     ref = exact.grad_total_logprob(dem, det).mean(axis=0)
     assert _rel(g, ref) < 1e-9, _rel(g, ref)
 
