@@ -372,6 +372,35 @@ def main():
         for n_u in nets_u:
             n_u.close()
 
+    # gradient of the mean log P with respect to every mechanism rate (td_grad_logprob):
+    # rotated d=7, 7 noisy rounds + 1 perfect, per-mechanism rates log-uniform in
+    # [1e-3, 1e-2]; each gradient shot decodes 1 + 2 x (rates in the network) virtual shots
+    if extra is not None:
+        from td_inputs import log_uniform_rates
+        dem_g = log_uniform_rates(rotated_phenomenological(7, 7, 0.005, 0.005), seed=5000)
+        g_shots = 16
+        dg, _ = sample_shots(dem_g, g_shots, seed=5001)
+        ddg = torch.from_numpy(dg).cuda()
+        gres, gvals = {}, {}
+        for name, prec in (("mixed", td.TD_FP32), ("fp64", td.TD_FP64)):
+            ng = td.Network.from_dem(dem_g, chi=8, chi_mps=8, precision=prec, mem_budget=32 << 30)
+            ng.grad_logprob(ddg[:1])        # host table of forced parameter objects + warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, gg = ng.grad_logprob(ddg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gres[name] = {"value": g_shots / (e0.elapsed_time(e1) / 1000.0), "unit": "gradient shots/s"}
+            gvals[name] = gg
+            ng.close()
+        gres["max_abs_dgrad_mixed_vs_fp64_rel_to_max"] = float(
+            (gvals["mixed"] - gvals["fp64"]).abs().max() / gvals["fp64"].abs().max())
+        gres["decodes_per_gradient_shot"] = 1 + 2 * dem_g.n_mech
+        gres["note"] = (f"{g_shots} shots, chi = chi_mps = 8, {dem_g.n_mech} rates; d mean log P / d p_j = "
+                        "(P_{x_j=1} - P_{x_j=0}) / P with every P from the decoder (exact without truncation)")
+        extra["grad_rotated_d7_7rounds_loguniform_chi8"] = gres
+
     # roofline of the dominant kernel (largest summed device time in the timed region)
     peaks = {}
     try:
