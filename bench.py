@@ -101,6 +101,18 @@ def max_over_ranks(value, world, device="cpu"):
     return float(t.item())
 
 
+def mean_over_ranks(vec, count, world, device="cpu"):
+    """Shot-weighted mean over the ranks of per-rank means (the gradient of the mean log P
+    when the shots are split across ranks: the one collective of the gradient path)."""
+    import torch
+    v = torch.as_tensor(vec, dtype=torch.float64, device=device).reshape(-1)
+    t = torch.cat([v * float(count), torch.tensor([float(count)], dtype=torch.float64, device=device)])
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t[:-1] / t[-1]
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -374,32 +386,37 @@ def main():
 
     # gradient of the mean log P with respect to every mechanism rate (td_grad_logprob):
     # rotated d=7, 7 noisy rounds + 1 perfect, per-mechanism rates log-uniform in
-    # [1e-3, 1e-2]; each gradient shot decodes 1 + 2 x (rates in the network) virtual shots
-    if extra is not None:
+    # [1e-3, 1e-2]; each gradient shot decodes 1 + 2 x (rates in the network) virtual shots.
+    # Every rank takes its own slice of the shots; the per-rank gradients are combined by one
+    # all-reduce (the only collective of the gradient path).
+    if not args.no_extra:
         from td_inputs import log_uniform_rates
         dem_g = log_uniform_rates(rotated_phenomenological(7, 7, 0.005, 0.005), seed=5000)
         g_shots = 16
-        dg, _ = sample_shots(dem_g, g_shots, seed=5001)
+        dg, _ = sample_shots(dem_g, g_shots, seed=5001, first_shot=replica_first_shot(rank, g_shots))
         ddg = torch.from_numpy(dg).cuda()
         gres, gvals = {}, {}
         for name, prec in (("mixed", td.TD_FP32), ("fp64", td.TD_FP64)):
             ng = td.Network.from_dem(dem_g, chi=8, chi_mps=8, precision=prec, mem_budget=32 << 30)
             ng.grad_logprob(ddg[:1])        # host table of forced parameter objects + warm-up
             torch.cuda.synchronize()
+            barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             _, gg = ng.grad_logprob(ddg)
             e1.record(stream)
             torch.cuda.synchronize()
-            gres[name] = {"value": g_shots / (e0.elapsed_time(e1) / 1000.0), "unit": "gradient shots/s"}
-            gvals[name] = gg
+            t_g = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
+            gvals[name] = mean_over_ranks(gg, g_shots, world, "cuda")
+            gres[name] = {"value": world * g_shots / t_g, "unit": "gradient shots/s"}
             ng.close()
         gres["max_abs_dgrad_mixed_vs_fp64_rel_to_max"] = float(
             (gvals["mixed"] - gvals["fp64"]).abs().max() / gvals["fp64"].abs().max())
         gres["decodes_per_gradient_shot"] = 1 + 2 * dem_g.n_mech
-        gres["note"] = (f"{g_shots} shots, chi = chi_mps = 8, {dem_g.n_mech} rates; d mean log P / d p_j = "
+        gres["note"] = (f"{g_shots} shots per GPU, chi = chi_mps = 8, {dem_g.n_mech} rates; d mean log P / d p_j = "
                         "(P_{x_j=1} - P_{x_j=0}) / P with every P from the decoder (exact without truncation)")
-        extra["grad_rotated_d7_7rounds_loguniform_chi8"] = gres
+        if extra is not None:
+            extra["grad_rotated_d7_7rounds_loguniform_chi8"] = gres
 
     # roofline of the dominant kernel (largest summed device time in the timed region)
     peaks = {}
