@@ -154,31 +154,46 @@ td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64
                                   void* stream);
 
 /* Gradient of the mean total log-probability (1/B) sum_b log P(m_b), P(m) = sum_L p_{m,L}
- * (Sec. 2.4), with respect to every mechanism rate; the paper has no gradient.
+ * (Sec. 2.4), with respect to every mechanism rate, by a reverse sweep (the paper has no
+ * gradient).  The value differentiated is the decoder's own log P: the Sec. 4 sweep at the
+ * network's chi and chi_mps, truncations included, so the gradient is consistent with the
+ * values (central differences of td_coset_logprob agree while no truncation decision
+ * changes; without truncation it is the exact gradient).
  *
- * P(m) is affine in each rate p_j (mechanism j is one weighted node of the network of
- * Sec. 3.4), so d log P / d p_j = (P_{x_j=1} - P_{x_j=0}) / P, where P_{x_j=x} is the
- * network with p_j set to x.  All three values are computed by this library's decoder (the
- * Sec. 4 sweep at the network's chi, chi_mps and precision): the call decodes every shot
- * once as is and twice per mechanism whose rate enters the network (each forced copy
- * replaces one parameter object: a site-local matrix, a gate's p or a readout), batched
- * as B * (1 + 2 n_forced) virtual shots in the network's waves.  Without truncation the
- * result is the exact gradient; with truncation each P is the decoder's estimate.
- * Mechanisms without detectors only mix the classes and get 0; a shot whose P comes out
- * 0 contributes nothing (the mean still divides by B).
+ * The call runs the forward sweep once more in FP64 (whatever the network's precision)
+ * with every intermediate site tensor kept and every truncation core and zip-up cut
+ * recorded, then walks it backwards, one block of threads per shot: the adjoint of each
+ * truncated SVD (the thin SVD over the nonzero singular values), of the kappa-basis
+ * doubling of each gate, of the environment weights and of the site-local operators.  Its
+ * result is the adjoint of every parameter object (site-local matrix, gate rate, readout),
+ * summed over shots and mapped to the rates on the host through the objects' exact
+ * dependence on each rate (each object is affine in each rate).  Mechanisms without
+ * detectors only mix the classes and get 0; a shot whose P comes out 0 contributes nothing
+ * (the mean still divides by B).
  *
  * det_dev: device uint8 [B][n_det]; p_dev: device double [n_mech] rates in [0, 1], or
  * NULL for the network's current rates.  A p_dev different from the current rates must
  * keep the network's structure (TD_ERR_INVALID otherwise) and becomes the network's rates
- * for this and later calls.  logP_dev: device double [B] (log P of each shot at the
- * rates); grad_dev: device double [n_mech].
- * The host builds the forced parameter objects (2 n_mech plans, cached while the rates do
- * not change) and synchronises `stream` before it does; the decodes and the reduction are
- * then queued on `stream` and the call returns without waiting for them.  Errors:
- * TD_ERR_INVALID (null buffers, rates outside [0, 1], B * (1 + 2 n_forced) >= 2^31),
- * TD_ERR_OOM, TD_ERR_CUDA. */
+ * for this and later calls.  logP_dev: device double [B] (log P of each shot at the rates,
+ * from the FP64 sweep); grad_dev: device double [n_mech].
+ * Memory: the first call allocates, beside the decoding workspace, the recording of up to
+ * min(wave, B, mem_budget / per-shot record) shots; larger B runs in several waves.  The
+ * call synchronises `stream` (the objects' dependence on the rates is built on the host,
+ * and the per-shot adjoints are summed there) and returns when the results are written.
+ * Errors: TD_ERR_INVALID (null buffers, rates outside [0, 1]), TD_ERR_OOM, TD_ERR_CUDA. */
 td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev,
                           double* logP_dev, double* grad_dev, void* stream);
+
+/* The same gradient by the affine identity d log P / d p_j = (P_{x_j=1} - P_{x_j=0}) / P, with
+ * P_{x_j=x} the network with p_j set to x and each of the three values from the decoder
+ * (at the network's chi, chi_mps and precision): B * (1 + 2 n_forced) decodes, batched as
+ * virtual shots that each replace one parameter object.  Without truncation it equals
+ * td_grad_logprob (both are exact); with truncation it differs from it by the truncation
+ * error of the forced networks.  Arguments, rates and errors as td_grad_logprob
+ * (TD_ERR_INVALID also when B * (1 + 2 n_forced) >= 2^31); the decodes are queued on
+ * `stream` and the call returns without waiting for them. */
+td_status td_grad_logprob_forced(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev,
+                                 double* logP_dev, double* grad_dev, void* stream);
 
 td_status td_network_get_info(const td_network* net, td_network_info* info);
 

@@ -124,10 +124,12 @@ class Network:
                                               C.c_void_p(out.data_ptr()), self._stream(stream)))
         return out
 
-    def grad_logprob(self, det, p=None, stream=None):
+    def grad_logprob(self, det, p=None, stream=None, method="reverse"):
         """(log P [B], d mean_b log P / d p [n_mech]) with P(m) = sum_L p_{m,L}, on det's
         device.  p: float64 rates on the device (None: the current rates); a given p
-        becomes the network's rates for later calls too."""
+        becomes the network's rates for later calls too.  method "reverse": the reverse
+        sweep (td_grad_logprob); "forced": the affine identity by forced decodes
+        (td_grad_logprob_forced)."""
         import torch
         self._check_det(det)
         B = det.shape[0]
@@ -138,8 +140,9 @@ class Network:
                 raise ValueError("p must be float64 [n_mech] on the detector buffer's device")
             p = p.contiguous()
         pp = C.c_void_p(p.data_ptr()) if p is not None else None
-        check(self._lib.td_grad_logprob(self._h, C.c_void_p(det.data_ptr()), B, pp, C.c_void_p(logP.data_ptr()),
-                                        C.c_void_p(grad.data_ptr()), self._stream(stream)))
+        fn = {"reverse": self._lib.td_grad_logprob, "forced": self._lib.td_grad_logprob_forced}[method]
+        check(fn(self._h, C.c_void_p(det.data_ptr()), B, pp, C.c_void_p(logP.data_ptr()),
+                 C.c_void_p(grad.data_ptr()), self._stream(stream)))
         return logP, grad
 
     def debug_sweep(self, det, n_gates, stream=None):

@@ -66,6 +66,18 @@ struct td_network {
   size_t d_vlogp_cap = 0;
   int32_t* d_act = nullptr;
   size_t d_act_cap = 0;
+  // reverse sweep: versioned descriptors, round tables, per-wave buffers (grad_wave shots)
+  td::GateDesc* d_hgates = nullptr;
+  td::LocalDesc* d_hlocals = nullptr;
+  td::FinalSite* d_hfinals = nullptr;
+  int32_t* d_round_first = nullptr;
+  int32_t* d_layer_round = nullptr;
+  int32_t grad_wave = 0;
+  double *d_hist = nullptr, *d_rec_core = nullptr, *d_rec_sc = nullptr, *d_rec_fin = nullptr, *d_adj_scr = nullptr,
+         *d_gfscr = nullptr, *d_Kbar = nullptr, *d_pbar = nullptr, *d_Rbar = nullptr, *d_glogp = nullptr,
+         *d_grad_tmp = nullptr;
+  td::AdjArgs adj{};
+  td::FinalArgs gfin{};
   td_dem dem_view(const double* p) const {
     td_dem d{};
     d.n_det = plan.n_det; d.n_mech = plan.n_mech; d.n_obs = n_obs;
@@ -545,8 +557,8 @@ static td_status prepare_overrides(td_network* net, const std::vector<double>& r
   return TD_OK;
 }
 
-td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev, double* logP_dev,
-                          double* grad_dev, void* stream) {
+td_status td_grad_logprob_forced(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev,
+                                 double* logP_dev, double* grad_dev, void* stream) {
   g_err.clear();
   td_status s = check_call(net, det_dev, B);
   if (s != TD_OK) return s;
@@ -604,6 +616,228 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
   }
   e = td::launch_grad_combine(net->d_vlogp, B, NV, net->d_act, n_mech, logP_dev, grad_dev, st);
   if (e != cudaSuccess) return cuda_fail(e, "gradient combine launch");
+  return TD_OK;
+}
+
+// ---- reverse sweep ----------------------------------------------------------------------
+// Buffers and layouts of the reverse sweep for waves of up to net->grad_wave shots.
+static td_status prepare_reverse(td_network* net, int64_t B) {
+  td::Plan& P = net->plan;
+  const int chi = P.chi, cm = P.chi_mps, Dm = P.max_final_D, cmx = std::max(cm, 2);
+  const int64_t max_site = (P.max_site_elems + 3) / 4 * 4;
+  const int64_t mA = net->fin.mps_stride;
+  const int64_t mC = (int64_t)cm * cmx * Dm * 2;
+  const int m_max = cm * Dm, n_max = cmx * Dm * 2;
+  const td::FinRecSlot ly((int)mC, (int)mA, m_max, n_max);
+  const int64_t fin_slot = (ly.size + 3) / 4 * 4;
+  const int64_t fin_stride = fin_slot * P.nx * P.ny;
+  const int64_t core_rec = td::core_rec_elems(chi);
+  // adjoint scratch per shot
+  int64_t acc = 0;
+  auto take = [&](int64_t n) { int64_t r = acc; acc += (n + 3) / 4 * 4; return r; };
+  td::AdjArgs& A = net->adj;
+  A = td::AdjArgs{};
+  A.max_site = max_site;
+  A.o_gbar = take(max_site * P.S);
+  A.o_xbar = take(2 * max_site);
+  A.o_r = take(max_site);
+  A.o_lambar = take((int64_t)P.n_bonds * chi);
+  A.o_core = take(td::CoreScr_elems(chi, max_site));
+  const int64_t mF = 2LL * Dm * Dm * Dm * Dm, mT1 = (int64_t)Dm * 2 * Dm * cmx * cm, mMN = (int64_t)m_max * n_max;
+  A.fo_F = take(mF); A.fo_Fb = take(mF);
+  A.fo_T1 = take(mT1); A.fo_T1b = take(mT1);
+  A.fo_M = take(mMN); A.fo_Mb = take(mMN);
+  A.fo_C0 = take(mMN); A.fo_C1 = take(mMN);
+  A.fo_A0 = take(mA * P.nx); A.fo_A1 = take(mA * P.nx);
+  A.fo_Ub = take((int64_t)m_max * cm); A.fo_W = take((int64_t)m_max * m_max); A.fo_J = take((int64_t)m_max * cm);
+  A.scr_stride = acc;
+  // FP64 final contraction of the recorded forward: work region in global scratch
+  td::FinalArgs& G = net->gfin;
+  G = net->fin;
+  G.use_smem = 0;
+  G.off_work = (net->fin.off_mps1 + mA * P.nx + 3) / 4 * 4;
+  G.scratch_elems = G.off_work + net->fin.work_elems;
+  G.rec_stride = fin_stride; G.rec_slot = fin_slot;
+  G.rec_mC = (int32_t)mC; G.rec_mA = (int32_t)mA; G.rec_m = m_max; G.rec_n = n_max;
+  const int64_t n_gates = (int64_t)P.gates.size();
+  const size_t per_shot = 8 * (size_t)(P.hist_shot_elems + n_gates * core_rec + (int64_t)P.T * P.S + fin_stride +
+                                       A.scr_stride + G.scratch_elems + (int64_t)P.T * P.S * 16 + n_gates + P.S * 8 + 2);
+  const size_t budget = net->opt.mem_budget ? net->opt.mem_budget : (size_t(16) << 30);
+  int64_t gw = std::min<int64_t>({(int64_t)net->wave, std::max<int64_t>(B, 1),
+                                   std::max<int64_t>(1, (int64_t)(budget / std::max<size_t>(per_shot, 1)))});
+  if (net->d_hist) return TD_OK;   // sized by the first call; later calls run in waves of grad_wave
+  auto res = [&](double*& ptr, int64_t n) { size_t c = 0; return net->reserve(ptr, c, (size_t)n); };
+  if (!res(net->d_hist, gw * P.hist_shot_elems) || !res(net->d_rec_core, std::max<int64_t>(n_gates, 1) * gw * core_rec) ||
+      !res(net->d_rec_sc, (int64_t)P.T * gw * P.S) || !res(net->d_rec_fin, gw * fin_stride) ||
+      !res(net->d_adj_scr, gw * A.scr_stride) || !res(net->d_gfscr, gw * G.scratch_elems) ||
+      !res(net->d_Kbar, gw * P.T * P.S * 16) || !res(net->d_pbar, gw * std::max<int64_t>(n_gates, 1)) ||
+      !res(net->d_Rbar, gw * P.S * 8) || !res(net->d_glogp, gw * 2))
+    return fail(TD_ERR_OOM, "reverse-sweep buffers");
+  if (!net->d_hgates) {
+    std::vector<int32_t> rf, lr;
+    int32_t nr = 0;
+    for (const td::LayerPlan& L : P.layers) {
+      lr.push_back(nr);
+      for (const td::Round& R : L.rounds) { rf.push_back(R.first); ++nr; }
+    }
+    lr.push_back(nr);
+    rf.push_back((int32_t)P.gates.size());
+    size_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+    if (!net->reserve(net->d_hgates, c1, std::max<size_t>(P.hist_gates.size(), 1)) ||
+        !net->reserve(net->d_hlocals, c2, P.hist_locals.size()) || !net->reserve(net->d_hfinals, c3, P.hist_finals.size()) ||
+        !net->reserve(net->d_round_first, c4, rf.size()) || !net->reserve(net->d_layer_round, c5, lr.size()))
+      return fail(TD_ERR_OOM, "reverse-sweep descriptors");
+    cudaError_t e;
+    if ((!P.hist_gates.empty() && (e = cudaMemcpy(net->d_hgates, P.hist_gates.data(), sizeof(td::GateDesc) * P.hist_gates.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(net->d_hlocals, P.hist_locals.data(), sizeof(td::LocalDesc) * P.hist_locals.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->d_hfinals, P.hist_finals.data(), sizeof(td::FinalSite) * P.hist_finals.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->d_round_first, rf.data(), sizeof(int32_t) * rf.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->d_layer_round, lr.data(), sizeof(int32_t) * lr.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess)
+      return cuda_fail(e, "reverse-sweep descriptor upload");
+  }
+  net->grad_wave = (int32_t)gw;
+  return TD_OK;
+}
+
+// The versioned descriptors carry the rates of the build; after a change of rates they are
+// refreshed from the plan (same structure, new K, p and R).
+static td_status refresh_hist_params(td_network* net, cudaStream_t st) {
+  td::Plan& P = net->plan;
+  for (size_t i = 0; i < P.hist_locals.size(); ++i) std::memcpy(P.hist_locals[i].K, P.locals[i].K, sizeof(P.locals[i].K));
+  for (size_t i = 0; i < P.hist_gates.size(); ++i) P.hist_gates[i].p = P.gates[i].p;
+  for (size_t i = 0; i < P.hist_finals.size(); ++i) std::memcpy(P.hist_finals[i].R, P.finals[i].R, sizeof(P.finals[i].R));
+  cudaError_t e;
+  if ((!P.hist_gates.empty() && (e = cudaMemcpyAsync(net->d_hgates, P.hist_gates.data(), sizeof(td::GateDesc) * P.hist_gates.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) ||
+      (e = cudaMemcpyAsync(net->d_hlocals, P.hist_locals.data(), sizeof(td::LocalDesc) * P.hist_locals.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(net->d_hfinals, P.hist_finals.data(), sizeof(td::FinalSite) * P.hist_finals.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(e, "reverse-sweep descriptor upload");
+  return TD_OK;
+}
+
+td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev, double* logP_dev,
+                          double* grad_dev, void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (!grad_dev || (B > 0 && !logP_dev)) return fail(TD_ERR_INVALID, "null output buffer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  td::Plan& P = net->plan;
+  const int32_t n_mech = P.n_mech, S = P.S, T = P.T, chi = P.chi;
+  const int64_t n_gates = (int64_t)P.gates.size();
+  std::vector<double> rates = net->rates;
+  cudaError_t e;
+  if (p_dev) {
+    e = cudaMemcpyAsync(rates.data(), p_dev, sizeof(double) * n_mech, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "rate copy");
+    for (int32_t j = 0; j < n_mech; ++j)
+      if (!(rates[j] >= 0.0 && rates[j] <= 1.0)) return fail(TD_ERR_INVALID, "rate outside [0, 1]");
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  s = prepare_overrides(net, rates, st);   // objects at the rates and at every forced rate
+  if (s != TD_OK) return s;
+  s = prepare_reverse(net, B);
+  if (s != TD_OK) return s;
+  s = refresh_hist_params(net, st);
+  if (s != TD_OK) return s;
+  std::vector<double> Ksum((size_t)T * S * 16, 0.0), psum((size_t)n_gates, 0.0), Rsum((size_t)S * 8, 0.0);
+  std::vector<double> hK, hp, hR;
+  const int64_t gw = net->grad_wave;
+  for (int64_t w0 = 0; w0 < B; w0 += gw) {
+    const int32_t Bw = (int32_t)std::min<int64_t>(gw, B - w0);
+    td::SweepArgs a{};
+    a.gamma = net->d_hist;
+    a.shot_elems = P.hist_shot_elems;
+    a.lam = net->d_lam;
+    a.logacc = net->d_logacc;
+    a.det = det_dev;
+    a.nbonds = P.n_bonds; a.chi = chi; a.nslots = net->nslots; a.n_det = P.n_det;
+    a.wave_first = (int32_t)w0;
+    a.B = Bw;
+    a.gram_cutoff = P.gram_cutoff; a.svd_cutoff = P.svd_cutoff; a.multiplet_rtol = P.multiplet_rtol;
+    a.rec_core = net->d_rec_core;
+    if ((e = td::launch_sweep_init<double, double>(a, net->d_hlocals, S, st)) != cudaSuccess) return cuda_fail(e, "init launch");
+    for (int32_t t = 0; t < T; ++t) {
+      a.layer = t;
+      a.rec_sc = net->d_rec_sc + (int64_t)t * Bw * S;
+      if ((e = td::launch_local<double, double>(a, net->d_hlocals + (int64_t)t * S, S, st)) != cudaSuccess)
+        return cuda_fail(e, "local launch");
+      for (const td::Round& rd : P.layers[t].rounds)
+        if ((e = td::launch_round<double, double>(a, net->d_hgates, rd, net->d_gram, net->d_tbuf, S, st)) != cudaSuccess)
+          return cuda_fail(e, "gate round launch");
+    }
+    td::FinalArgs f = net->gfin;
+    f.gamma = net->d_hist; f.shot_elems = P.hist_shot_elems; f.lam = net->d_lam; f.logacc = net->d_logacc;
+    f.sites = net->d_hfinals; f.grid_site = net->d_grid; f.scratch = net->d_gfscr; f.Z = net->d_Z;
+    f.nbonds = P.n_bonds; f.chi = chi; f.nslots = net->nslots; f.slot = S + P.n_bonds;
+    f.nx = P.nx; f.ny = P.ny; f.chi_mps = P.chi_mps; f.B = Bw;
+    f.svd_cutoff = P.svd_cutoff; f.multiplet_rtol = P.multiplet_rtol;
+    f.rec = net->d_rec_fin;
+    if ((e = td::launch_final<double, double>(f, st)) != cudaSuccess) return cuda_fail(e, "final launch");
+    td::FinalizeArgs z{};
+    z.Z = net->d_Z; z.logacc = net->d_logacc; z.det = det_dev + w0 * P.n_det; z.logp = net->d_glogp;
+    z.nslots = net->nslots; z.n_det = P.n_det; z.wave_first = 0; z.B = Bw; z.offset_all = P.offset_all;
+    for (int i = 0; i < 4; ++i) z.mix[i] = P.glob_mix[i];
+    if ((e = td::launch_finalize(z, st)) != cudaSuccess) return cuda_fail(e, "finalize launch");
+    if ((e = td::launch_grad_combine(net->d_glogp, Bw, 1, nullptr, 0, logP_dev + w0, nullptr, st)) != cudaSuccess)
+      return cuda_fail(e, "log P launch");
+    td::AdjArgs A = net->adj;
+    A.hist = net->d_hist; A.hist_elems = P.hist_shot_elems; A.lam = net->d_lam; A.Z = net->d_Z;
+    A.rec_core = net->d_rec_core; A.rec_sc = net->d_rec_sc; A.rec_fin = net->d_rec_fin;
+    A.fin_stride = f.rec_stride; A.fin_slot = f.rec_slot;
+    A.fin_mC = f.rec_mC; A.fin_mA = f.rec_mA; A.fin_m = f.rec_m; A.fin_n = f.rec_n;
+    A.gates = net->d_hgates; A.locals = net->d_hlocals; A.finals = net->d_hfinals; A.grid_site = net->d_grid;
+    A.round_first = net->d_round_first; A.layer_round = net->d_layer_round;
+    A.det = det_dev; A.n_det = P.n_det; A.wave_first = (int32_t)w0;
+    A.scratch = net->d_adj_scr;
+    A.S = S; A.T = T; A.nbonds = P.n_bonds; A.chi = chi; A.nx = P.nx; A.ny = P.ny; A.B = Bw;
+    A.n_gates = (int32_t)n_gates; A.max_final_D = P.max_final_D; A.mps_stride = (int32_t)net->fin.mps_stride;
+    A.Kbar = net->d_Kbar; A.pbar = net->d_pbar; A.Rbar = net->d_Rbar;
+    if ((e = td::launch_adjoint(A, 256, st)) != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    hK.resize((size_t)Bw * T * S * 16); hp.resize((size_t)Bw * n_gates); hR.resize((size_t)Bw * S * 8);
+    if ((e = cudaMemcpyAsync(hK.data(), net->d_Kbar, sizeof(double) * hK.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (n_gates > 0 && (e = cudaMemcpyAsync(hp.data(), net->d_pbar, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(hR.data(), net->d_Rbar, sizeof(double) * hR.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return cuda_fail(e, "adjoint copy");
+    for (int32_t b = 0; b < Bw; ++b) {
+      for (size_t i = 0; i < Ksum.size(); ++i) Ksum[i] += hK[(size_t)b * Ksum.size() + i];
+      for (size_t i = 0; i < psum.size(); ++i) psum[i] += hp[(size_t)b * psum.size() + i];
+      for (size_t i = 0; i < Rsum.size(); ++i) Rsum[i] += hR[(size_t)b * Rsum.size() + i];
+    }
+  }
+  // rates: d mean log P / d p_j = sum over objects of object-bar . (object(p_j=1) - object(p_j=0)) / B
+  std::vector<double> grad(n_mech, 0.0);
+  for (int32_t j = 0; j < n_mech && B > 0; ++j) {
+    const int32_t o0 = net->ovr_of[2 * (size_t)j], o1 = net->ovr_of[2 * (size_t)j + 1];
+    if (!o0 && !o1) continue;
+    const td::Override& ref = net->ovr_host[o1 ? o1 : o0];
+    double acc = 0.0;
+    if (ref.kind == td::kOvrLocal) {
+      const double* base = P.locals[ref.target].K;
+      const double* v1 = o1 ? net->ovr_host[o1].val : base;
+      const double* v0 = o0 ? net->ovr_host[o0].val : base;
+      for (int e2 = 0; e2 < 16; ++e2) acc += Ksum[(size_t)ref.target * 16 + e2] * (v1[e2] - v0[e2]);
+    } else if (ref.kind == td::kOvrGate) {
+      const double base = P.gates[ref.target].p;
+      const double v1 = o1 ? net->ovr_host[o1].val[0] : base, v0 = o0 ? net->ovr_host[o0].val[0] : base;
+      acc = psum[ref.target] * (v1 - v0);
+    } else if (ref.kind == td::kOvrRead) {
+      const double* base = P.finals[ref.target].R;
+      const double* v1 = o1 ? net->ovr_host[o1].val : base;
+      const double* v0 = o0 ? net->ovr_host[o0].val : base;
+      for (int e2 = 0; e2 < 8; ++e2) acc += Rsum[(size_t)ref.target * 8 + e2] * (v1[e2] - v0[e2]);
+    }
+    grad[j] = acc / (double)B;
+  }
+  if (n_mech > 0) {
+    e = cudaMemcpyAsync(grad_dev, grad.data(), sizeof(double) * n_mech, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "gradient copy");
+  }
   return TD_OK;
 }
 

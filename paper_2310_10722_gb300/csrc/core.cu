@@ -206,6 +206,18 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
   double* TT = RF;           // scratch free once theta is formed (R is consumed)
   const int rAp = rk[0], rA = rk[0] + rk[1], rBp = rk[2], rB = rk[2] + rk[3];
   double* tout = tbuf + item * 4 * chi * chi;
+  // record for the reverse sweep: ranks, old lambda, R factors and right inverses
+  double* rec = a.rec_core ? a.rec_core + ((int64_t)(a.gate_base + gi) * a.B + b) * core_rec_elems(chi) : nullptr;
+  const int CC = chi * chi, L2 = 2 * chi;
+  if (rec) {
+    if (tm.tid < 4) rec[tm.tid] = rk[tm.tid];
+    if (tm.tid == 4) { rec[4] = 0.0; rec[5] = 0.0; }
+    for (int w = tm.tid; w < D; w += tm.nt) rec[8 + w] = sm.lam[w];
+    for (int w = tm.tid; w < 4 * DD; w += tm.nt) {
+      rec[8 + chi + (w / DD) * CC + w % DD] = RF[w];
+      rec[8 + chi + 4 * CC + (w / DD) * CC + w % DD] = RI[w];
+    }
+  }
   if (rA == 0 || rB == 0) {            // zero state: this shot has probability 0
     for (int w = tm.tid; w < 4 * chi * chi; w += tm.nt) tout[w] = 0.0;
     for (int w = tm.tid; w < Dn; w += tm.nt) lamg[w] = 0.0;
@@ -255,6 +267,16 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
     for (int w = tm.tid; w < Dn; w += tm.nt) lamg[w] = 0.0;
     if (tm.tid == 0) a.logacc[(int64_t)b * a.nslots + S + gd.bond] = -INFINITY;
     return;
+  }
+  if (rec) {
+    double* rUS = rec + 8 + chi + 8 * CC;
+    double* rV = rUS + L2 * L2;
+    double* rsv = rV + L2 * L2;
+    double* rord = rsv + L2;
+    for (int w = tm.tid; w < rA * rB; w += tm.nt) rUS[(w / rA) * L2 + w % rA] = TH[(w / rA) * ldt + w % rA];
+    for (int w = tm.tid; w < rB * rB; w += tm.nt) rV[(w / rB) * L2 + w % rB] = VV[(w / rB) * ldv + w % rB];
+    for (int w = tm.tid; w < rB; w += tm.nt) { rsv[w] = sm.sv[w]; rord[w] = sm.order[w]; }
+    if (tm.tid == 0) { rec[4] = k; rec[5] = s0; }
   }
   for (int j = tm.tid; j < k; j += tm.nt) sm.aux[j] = 1.0 / sm.sv[sm.order[j]];
   tm.sync();

@@ -119,6 +119,20 @@ __global__ void k_final(FinalArgs fa) {
       (void)cA;
       // T1[l][p][d][bb][j] = sum_a C[j][a][l][p] A[a][d][bb]  (j fastest: the lanes of one
       // warp below read four j values of the same (l, p, d, bb) from distinct banks)
+      double* rs = nullptr;    // this column's record slot (reverse sweep)
+      if constexpr (sizeof(R) == 8) {
+        if (fa.rec) {
+          rs = fa.rec + (int64_t)b * fa.rec_stride + (int64_t)(y * nx + x) * fa.rec_slot;
+          const FinRecSlot ly(fa.rec_mC, fa.rec_mA, fa.rec_m, fa.rec_n);
+          for (int w = tm.tid; w < cJ * aL * cL * 2; w += tm.nt) rs[ly.C + w] = double(C[w]);
+          for (int w = tm.tid; w < aL * aD * aR; w += tm.nt) rs[ly.A + w] = double(A[w]);
+          if (tm.tid == 0) {
+            rs[1] = cJ; rs[2] = aL; rs[3] = cL; rs[4] = aD; rs[5] = aR;
+            rs[6] = L; rs[7] = Rr; rs[8] = U;
+            rs[0] = (x == nx - 1) ? 2 : (y == ny - 1 ? 1 : 0);
+          }
+        }
+      }
       R* T1 = W;
       const int n1 = cJ * L * 2 * aD * aR;
       for (int w = tm.tid; w < n1; w += tm.nt) {
@@ -175,6 +189,19 @@ __global__ void k_final(FinalArgs fa) {
         }
         tm.sync();
         const int k = meta[0];
+        if constexpr (sizeof(R) == 8) {
+          if (rs) {
+            const FinRecSlot ly(fa.rec_mC, fa.rec_mA, fa.rec_m, fa.rec_n);
+            for (int w = tm.tid; w < m * m; w += tm.nt) rs[ly.V + w] = double(V[(w / m) * ldv + w % m]);
+            for (int w = tm.tid; w < n * m; w += tm.nt) rs[ly.MT + w] = double(MT[(w / n) * ldm + w % n]);
+            for (int w = tm.tid; w < m; w += tm.nt) { rs[ly.sv + w] = double(sv[w]); rs[ly.ord + w] = ord[w]; }
+            if (tm.tid == 0) {
+              int e2r = 0;
+              if (k > 0) frexp(double(sv[ord[0]]), &e2r);
+              rs[9] = m; rs[10] = n; rs[11] = k; rs[12] = e2r;
+            }
+          }
+        }
         if (k == 0) {
           if (tm.tid == 0) logsum_s = -INFINITY;
           for (int w = tm.tid; w < m; w += tm.nt) An[w] = R(0);
@@ -205,6 +232,7 @@ __global__ void k_final(FinalArgs fa) {
         tm.sync();
       } else if (x < nx - 1) {
         // last row: U == 1, no truncation; the carry takes the whole contraction
+        if (rs && tm.tid == 0) { rs[9] = m; rs[10] = n; }
         for (int w = tm.tid; w < m * n; w += tm.nt) {
           const int ju = w / n, c = w % n;
           Cn[w] = MT[ju * ldm + c];
@@ -237,6 +265,7 @@ __global__ void k_final(FinalArgs fa) {
               logsum_s = -INFINITY;
             }
             slam[0] = mx > R(0) ? R(ldexp(1.0, -e2)) : R(0);
+            if (rs) { rs[9] = m; rs[10] = n; rs[12] = e2; }
             mdim[cur ^ 1][x][0] = cJ; mdim[cur ^ 1][x][1] = U; mdim[cur ^ 1][x][2] = 2;
           }
         }

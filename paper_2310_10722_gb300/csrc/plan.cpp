@@ -319,6 +319,7 @@ td_status build_plan(const td_dem& dem, const td_layout& layout, const td_option
       ld.det = det_at[(size_t)t * S + s];
       ld.rest = (int32_t)(site_size(s, dims) / plan.P[s]);
       ld.off = buf_off(s, cur[s]);
+      ld.out_off = ld.off;
       double K[16], post[16];
       std::memcpy(K, &pre[((size_t)t * S + s) * 16], sizeof(K));
       if (t > 0) {
@@ -396,6 +397,45 @@ td_status build_plan(const td_dem& dem, const td_layout& layout, const td_option
   }
   plan.final_dims = dims;
   for (int32_t d : dims) plan.max_final_D = std::max(plan.max_final_D, d);
+
+  // versioned layout: every local operator and gate output gets a new slot
+  {
+    int64_t hacc = 0;
+    auto slot = [&](int64_t n) { int64_t r = hacc; hacc += (n + 3) / 4 * 4; return r; };
+    std::vector<int64_t> ver(S);
+    std::vector<int32_t> hd(plan.n_bonds, 1);
+    for (int32_t s = 0; s < S; ++s) ver[s] = slot(site_size(s, hd));
+    plan.hist_locals.clear();
+    plan.hist_gates.clear();
+    size_t gi = 0;
+    for (int32_t t = 0; t < T; ++t) {
+      for (int32_t s = 0; s < S; ++s) {
+        LocalDesc ld = plan.locals[(size_t)t * S + s];
+        ld.off = ver[s];
+        ld.out_off = slot(site_size(s, hd));
+        ver[s] = ld.out_off;
+        plan.hist_locals.push_back(ld);
+      }
+      for (const Round& R : plan.layers[t].rounds)
+        for (int32_t q = 0; q < R.count; ++q, ++gi) {
+          GateDesc g = plan.gates[gi];
+          const int32_t ends[2] = {g.side[0].site, g.side[1].site};
+          hd[g.bond] = g.Dn;
+          for (int side = 0; side < 2; ++side) {
+            SideDesc& sd = g.side[side];
+            sd.in_off = ver[ends[side]];
+            sd.out_off = slot(site_size(ends[side], hd));
+            ver[ends[side]] = sd.out_off;
+          }
+          plan.hist_gates.push_back(g);
+        }
+    }
+    plan.hist_finals = plan.finals;
+    for (int32_t s = 0; s < S; ++s) plan.hist_finals[s].off = ver[s];
+    plan.hist_shot_elems = hacc;
+    plan.max_site_elems = 1;
+    for (int32_t s = 0; s < S; ++s) plan.max_site_elems = std::max(plan.max_site_elems, maxsize[s]);
+  }
   return TD_OK;
 }
 

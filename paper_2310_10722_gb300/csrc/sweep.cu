@@ -68,7 +68,8 @@ __global__ void k_local(SweepArgs a, const LocalDesc* __restrict__ locals) {
     K[threadIdx.x] = Ksrc[(row ^ m) * d.P + col];     // rows of X^m K
   }
   __syncthreads();
-  T* g = reinterpret_cast<T*>(a.gamma) + (int64_t)b * a.shot_elems + d.off;
+  const T* g = reinterpret_cast<const T*>(a.gamma) + (int64_t)b * a.shot_elems + d.off;
+  T* go = reinterpret_cast<T*>(a.gamma) + (int64_t)b * a.shot_elems + d.out_off;
   double mx = 0.0;
   for (int r = threadIdx.x; r < d.rest; r += blockDim.x) {
     double v[kMaxPhys];
@@ -89,12 +90,13 @@ __global__ void k_local(SweepArgs a, const LocalDesc* __restrict__ locals) {
     for (int i = 0; i < d.P; ++i) {
       double acc = 0.0;
       for (int k = 0; k < d.P; ++k) acc += K[i * d.P + k] * v[k];
-      g[(int64_t)i * d.rest + r] = T(acc * sc);
+      go[(int64_t)i * d.rest + r] = T(acc * sc);
     }
   }
   if (threadIdx.x == 0) {
     double* la = a.logacc + (int64_t)b * a.nslots + s;
     *la += (mx > 0.0) ? double(e2) * 0.69314718055994530942 : -INFINITY;
+    if (a.rec_sc) a.rec_sc[(int64_t)b * gridDim.x + s] = sc;
   }
 }
 

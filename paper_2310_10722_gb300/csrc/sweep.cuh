@@ -24,7 +24,16 @@ struct SweepArgs {
   const Override* ovr;
   int32_t layer;            // current layer (local operators)
   int32_t gate_base;        // global index of the round's first gate (core)
+  // recording for the reverse sweep (null otherwise)
+  double* rec_sc;           // [B][S] scale of this layer's site-local operators
+  double* rec_core;         // [gates][B][kCoreRec(chi)] truncation cores (indexed by global gate)
 };
+
+// Per-gate record of the truncation core for the reverse sweep (doubles), Dm = chi:
+// meta[8] (rk0..3, k, s0, unused), lam_old[Dm], R[4][Dm*Dm] (rows r x D, ld D, before the
+// lambda scaling), Rinv[4][Dm*Dm] (D x r, ld D), U S [(2Dm)(2Dm)] (theta V after the Jacobi
+// sweeps, column-major ld 2Dm, unsorted columns), V [(2Dm)(2Dm)] (same), sv[2Dm], order[2Dm].
+__host__ __device__ inline int64_t core_rec_elems(int Dm) { return 8 + Dm + 8LL * Dm * Dm + 8LL * Dm * Dm + 4 * Dm + 8; }
 
 // Detector row and override of shot b of a wave (plain decode: row wave_first + b, none).
 __device__ __forceinline__ int vshot_row(const VShot* vs, int wave_first, int b) {
@@ -60,7 +69,60 @@ struct FinalArgs {
   const VShot* vs;           // gradient pass: virtual shots and overrides (null otherwise)
   const Override* ovr;
   int32_t wave_first;
+  // recording for the reverse sweep (FP64 only; null otherwise): per shot rec_stride
+  // doubles, one slot of rec_slot doubles per (row, column); see FinRecSlot
+  double* rec;
+  int64_t rec_stride, rec_slot;
+  int32_t rec_mC, rec_mA, rec_m, rec_n;   // capacities: carry, MPS tensor, cut rows, cut columns
 };
+
+// Layout of one (row, column) slot of the final-contraction record: meta[16] = (kind,
+// cJ, aL, cL, aD, aR, L, Rr, U, m, n, k, e2; kind 0 cut, 1 last row, 2 last column), the
+// carry C [cJ][aL][cL][2], the MPS tensor A [aL][aD][aR], then for a cut: the left singular
+// vectors V (m x m, column-major ld m, unsorted), M^T after the Jacobi sweeps (n x m,
+// column-major ld n), the column norms sv[m] and the order[m].
+struct FinRecSlot {
+  int64_t C, A, V, MT, sv, ord, size;
+  __host__ __device__ FinRecSlot(int mC, int mA, int m, int n) {
+    C = 16; A = C + mC; V = A + mA; MT = V + (int64_t)m * m; sv = MT + (int64_t)n * m; ord = sv + m; size = ord + m;
+  }
+};
+
+// Reverse sweep (adjoint.cu): one block per shot of the wave, FP64.
+struct AdjArgs {
+  const double* hist;          // [B][hist_elems] forward site tensors, versioned layout
+  int64_t hist_elems;
+  double* lam;                 // [B][nbonds][chi] lambda after the sweep (restored backwards)
+  const double* Z;             // [B][2] final contraction values
+  const double* rec_core;      // [n_gates][B][core_rec_elems(chi)]
+  const double* rec_sc;        // [T][B][S] scales of the site-local operators
+  const double* rec_fin;       // [B][fin_stride] final-contraction record
+  int64_t fin_stride, fin_slot;
+  int32_t fin_mC, fin_mA, fin_m, fin_n;
+  const GateDesc* gates;       // versioned gate descriptors
+  const LocalDesc* locals;     // versioned local descriptors [T * S]
+  const FinalSite* finals;     // versioned final sites [S]
+  const int32_t* grid_site;    // [ny][nx]
+  const int32_t* round_first;  // [n_rounds + 1] first gate of every round, in sweep order
+  const int32_t* layer_round;  // [T + 1] first round of every layer
+  const uint8_t* det;
+  int32_t n_det, wave_first;
+  double* scratch;             // [B][scr_stride]
+  int64_t scr_stride;
+  int64_t o_gbar, o_xbar, o_r, o_lambar, o_core, o_fin;   // offsets in a shot's scratch
+  int64_t max_site;            // elements per site slot of gbar
+  int64_t fo_F, fo_Fb, fo_T1, fo_T1b, fo_M, fo_Mb, fo_C0, fo_C1, fo_A0, fo_A1, fo_Ub, fo_W, fo_J;  // final scratch
+  int32_t S, T, nbonds, chi, nx, ny, B, n_gates, max_final_D, mps_stride;
+  double* Kbar;                // [B][T * S][16]
+  double* pbar;                // [B][n_gates]
+  double* Rbar;                // [B][S][8]
+};
+cudaError_t launch_adjoint(const AdjArgs& a, int threads, cudaStream_t st);
+// Scratch of the per-gate core adjoint (doubles) for bond cap chi and rows up to max_oi.
+inline int64_t CoreScr_elems(int chi, int64_t max_oi) {
+  const int64_t L2 = 2 * chi;
+  return 2 * L2 * chi + 2 * L2 * L2 + 4 * L2 * chi + 5 * L2 * L2 + 2 * L2 * L2 + 2 * chi * L2 + 4 * chi + max_oi;
+}
 
 struct FinalizeArgs {
   const double* Z;

@@ -53,6 +53,7 @@ struct LocalDesc {
   int32_t rest;         // product of the site's current bond dims
   int32_t pad;
   int64_t off;          // element offset of the current tensor in a shot block
+  int64_t out_off;      // where the result goes (== off: in place)
   double K[kMaxPhys * kMaxPhys];
 };
 
@@ -117,6 +118,14 @@ struct Plan {
   int64_t shot_elems = 0;                // PEPS elements per shot (both buffers of all sites)
   int32_t max_round_gates = 0;
   int32_t max_final_D = 1;               // largest bond after the sweep
+  // Versioned layout of the reverse sweep: the same schedule with every site-local
+  // operator and every gate writing a new copy of its site tensors, so that every
+  // intermediate tensor of the forward sweep is kept (hist_shot_elems per shot).
+  std::vector<LocalDesc> hist_locals;    // off = input version, out_off = output version
+  std::vector<GateDesc> hist_gates;      // in_off / out_off = versions
+  std::vector<FinalSite> hist_finals;    // off = last version
+  int64_t hist_shot_elems = 0;
+  int64_t max_site_elems = 0;            // largest site tensor of the sweep (elements)
 };
 
 // Build the plan from the ABI structures.  Returns TD_OK or an error with `err` set.
