@@ -384,37 +384,55 @@ def main():
         for n_u in nets_u:
             n_u.close()
 
-    # gradient of the mean log P with respect to every mechanism rate (td_grad_logprob):
-    # rotated d=7, 7 noisy rounds + 1 perfect, per-mechanism rates log-uniform in
-    # [1e-3, 1e-2]; each gradient shot decodes 1 + 2 x (rates in the network) virtual shots.
-    # Every rank takes its own slice of the shots; the per-rank gradients are combined by one
-    # all-reduce (the only collective of the gradient path).
+    # gradient of the mean log P with respect to every mechanism rate: rotated d=7, 7 noisy
+    # rounds + 1 perfect, per-mechanism rates log-uniform in [1e-3, 1e-2], 1024 shots per
+    # GPU, by the reverse sweep (td_grad_logprob); every rank takes its own slice of the shots
+    # and the per-rank gradients are combined by one all-reduce (the only collective of the
+    # gradient path).  Beside it, the forced-rate gradient (td_grad_logprob_forced, 1 + 2 x
+    # 560 decodes per shot) on 16 of the shots.
     if not args.no_extra:
         from td_inputs import log_uniform_rates
         dem_g = log_uniform_rates(rotated_phenomenological(7, 7, 0.005, 0.005), seed=5000)
-        g_shots = 16
+        g_shots = 1024
         dg, _ = sample_shots(dem_g, g_shots, seed=5001, first_shot=replica_first_shot(rank, g_shots))
         ddg = torch.from_numpy(dg).cuda()
-        gres, gvals = {}, {}
-        for name, prec in (("mixed", td.TD_FP32), ("fp64", td.TD_FP64)):
-            ng = td.Network.from_dem(dem_g, chi=8, chi_mps=8, precision=prec, mem_budget=32 << 30)
-            ng.grad_logprob(ddg[:1])        # host table of forced parameter objects + warm-up
-            torch.cuda.synchronize()
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            _, gg = ng.grad_logprob(ddg)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_g = max_over_ranks(e0.elapsed_time(e1) / 1000.0, world, "cuda")
-            gvals[name] = mean_over_ranks(gg, g_shots, world, "cuda")
-            gres[name] = {"value": world * g_shots / t_g, "unit": "gradient shots/s"}
-            ng.close()
-        gres["max_abs_dgrad_mixed_vs_fp64_rel_to_max"] = float(
-            (gvals["mixed"] - gvals["fp64"]).abs().max() / gvals["fp64"].abs().max())
-        gres["decodes_per_gradient_shot"] = 1 + 2 * dem_g.n_mech
-        gres["note"] = (f"{g_shots} shots per GPU, chi = chi_mps = 8, {dem_g.n_mech} rates; d mean log P / d p_j = "
-                        "(P_{x_j=1} - P_{x_j=0}) / P with every P from the decoder (exact without truncation)")
+        ng = td.Network.from_dem(dem_g, chi=8, chi_mps=8, precision=td.TD_FP64, mem_budget=64 << 30)
+        ng.grad_logprob(ddg)                # allocations, forced-object tables, warm-up
+        ng.coset_logprob(ddg)
+        torch.cuda.synchronize()
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        lpg, gg = ng.grad_logprob(ddg)
+        ev[1].record(stream)
+        ng.coset_logprob(ddg)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        t_g = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1000.0, world, "cuda")
+        t_d = max_over_ranks(ev[1].elapsed_time(ev[2]) / 1000.0, world, "cuda")
+        g_all = mean_over_ranks(gg, g_shots, world, "cuda")
+        gres = {"value": world * g_shots / t_g, "unit": "gradient shots/s",
+                "seconds_per_1024_shots": t_g, "decode_seconds_same_shots_fp64": t_d,
+                "gradient_over_decode_time": t_g / t_d, "rates": dem_g.n_mech,
+                "grad_abs_max": float(g_all.abs().max())}
+        # forced-rate gradient on 16 shots (mixed-precision decodes) and the reverse sweep on
+        # the same shots: they differ by the truncation error of the forced networks only
+        nf = td.Network.from_dem(dem_g, chi=8, chi_mps=8, precision=td.TD_FP32, mem_budget=32 << 30)
+        nf.grad_logprob(ddg[:1], method="forced")
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        _, gf = nf.grad_logprob(ddg[:16], method="forced")
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        _, gr16 = ng.grad_logprob(ddg[:16])
+        gres["forced_rate_method"] = {"value": 16 / (ev[0].elapsed_time(ev[1]) / 1000.0), "unit": "gradient shots/s",
+                                      "decodes_per_shot": 1 + 2 * dem_g.n_mech,
+                                      "max_abs_diff_vs_reverse_rel_to_max": float((gf - gr16).abs().max()
+                                                                                  / gr16.abs().max())}
+        gres["note"] = (f"{g_shots} shots per GPU, chi = chi_mps = 8 (chi = 32 of the workload is out of reach: "
+                        "~7 min per decode); reverse sweep in FP64: recorded forward + per-shot adjoint")
+        ng.close()
+        nf.close()
         if extra is not None:
             extra["grad_rotated_d7_7rounds_loguniform_chi8"] = gres
 

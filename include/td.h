@@ -176,8 +176,9 @@ td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64
  * keep the network's structure (TD_ERR_INVALID otherwise) and becomes the network's rates
  * for this and later calls.  logP_dev: device double [B] (log P of each shot at the rates,
  * from the FP64 sweep); grad_dev: device double [n_mech].
- * Memory: the first call allocates, beside the decoding workspace, the recording of up to
- * min(wave, B, mem_budget / per-shot record) shots; larger B runs in several waves.  The
+ * Memory: beside the decoding workspace, the recording of up to min(wave, B, mem_budget /
+ * per-shot record) shots, allocated by the first call and grown by a later call with a
+ * larger B; a B above mem_budget / per-shot record runs in several waves.  The
  * call synchronises `stream` (the objects' dependence on the rates is built on the host,
  * and the per-shot adjoints are summed there) and returns when the results are written.
  * Errors: TD_ERR_INVALID (null buffers, rates outside [0, 1]), TD_ERR_OOM, TD_ERR_CUDA. */

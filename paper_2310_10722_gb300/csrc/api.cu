@@ -665,7 +665,15 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
   const size_t budget = net->opt.mem_budget ? net->opt.mem_budget : (size_t(16) << 30);
   int64_t gw = std::min<int64_t>({(int64_t)net->wave, std::max<int64_t>(B, 1),
                                    std::max<int64_t>(1, (int64_t)(budget / std::max<size_t>(per_shot, 1)))});
-  if (net->d_hist) return TD_OK;   // sized by the first call; later calls run in waves of grad_wave
+  if (net->d_hist && gw <= net->grad_wave) return TD_OK;   // smaller calls reuse the buffers
+  for (double** pp : {&net->d_hist, &net->d_rec_core, &net->d_rec_sc, &net->d_rec_fin, &net->d_adj_scr, &net->d_gfscr,
+                      &net->d_Kbar, &net->d_pbar, &net->d_Rbar, &net->d_glogp})
+    if (*pp) {
+      cudaFree(*pp);
+      net->allocs.erase(std::remove(net->allocs.begin(), net->allocs.end(), (void*)*pp), net->allocs.end());
+      *pp = nullptr;
+    }
+  net->grad_wave = 0;
   auto res = [&](double*& ptr, int64_t n) { size_t c = 0; return net->reserve(ptr, c, (size_t)n); };
   if (!res(net->d_hist, gw * P.hist_shot_elems) || !res(net->d_rec_core, std::max<int64_t>(n_gates, 1) * gw * core_rec) ||
       !res(net->d_rec_sc, (int64_t)P.T * gw * P.S) || !res(net->d_rec_fin, gw * fin_stride) ||
