@@ -74,25 +74,58 @@ __device__ __forceinline__ double env_weight(const SideDesc& sd, int o, int i, c
 }
 
 // Adds sum over rows (o, i) of r[o * inner + i] / lambda to lambda-bar of every other bond
-// of the side, at the row's digit (one thread per (slot, digit); rows in order).
+// of the side, at the row's digit.  A row index oi = o * inner + i is a mixed-radix number
+// over the side's other bonds (in slot order, the last fastest), so the rows of digit d of
+// slot k are oi = h * (dim_k * stride_k) + d * stride_k + l.  Every (slot, digit) gets
+// blockDim / n_out threads; their partial sums are added in a fixed order (red: >= blockDim
+// doubles of shared memory).
 __device__ void env_lambar(const SideDesc& sd, const double* r, const double* lam, double* lambar, int chi,
-                           double sign) {
+                           double sign, double* red) {
   const int OI = sd.outer * sd.inner;
-  for (int w = threadIdx.x; w < kMaxBonds * chi; w += blockDim.x) {
-    const int k = w / chi, idx = w % chi;
-    if (k >= sd.nb || k == sd.pos || idx >= sd.dims[k]) continue;
-    const double l = lam[sd.bond[k] * chi + idx];
-    if (!(l > 0.0)) continue;
-    double acc = 0.0;
-    for (int oi = 0; oi < OI; ++oi) {
-      int dig[kMaxBonds];
-      env_weight(sd, oi / sd.inner, oi % sd.inner, lam, chi, dig);
-      if (dig[k] == idx) acc += r[oi];
+  int stride[kMaxBonds], first[kMaxBonds + 1];
+  int n_out = 0;
+  {
+    int acc = 1;
+    for (int k = kMaxBonds - 1; k >= 0; --k) {
+      stride[k] = acc;
+      if (k < sd.nb && k != sd.pos) acc *= sd.dims[k];
     }
-    lambar[sd.bond[k] * chi + idx] += sign * acc / l;
+    for (int k = 0; k < kMaxBonds; ++k) {
+      first[k] = n_out;
+      if (k < sd.nb && k != sd.pos) n_out += sd.dims[k];
+    }
+    first[kMaxBonds] = n_out;
   }
+  if (n_out == 0) return;
+  const int parts = (int)blockDim.x / n_out;   // >= 1: n_out <= 3 * chi <= 96 < blockDim
+  const int t = threadIdx.x;
+  double acc = 0.0;
+  int k = -1, d = 0;
+  if (t < parts * n_out) {
+    const int o = t % n_out, part = t / n_out;
+    for (int kk = 0; kk < kMaxBonds; ++kk)
+      if (kk < sd.nb && kk != sd.pos && o >= first[kk] && o < first[kk] + sd.dims[kk]) { k = kk; d = o - first[kk]; }
+    const int dk = sd.dims[k], sk = stride[k];
+    const int cnt = OI / dk;
+    for (int e = part; e < cnt; e += parts) {
+      const int h = e / sk, l = e % sk;
+      acc += r[h * dk * sk + d * sk + l];
+    }
+  }
+  __syncthreads();
+  red[t] = acc;
+  __syncthreads();
+  if (t < n_out) {
+    double tot = 0.0;
+    for (int part = 0; part < parts; ++part) tot += red[part * n_out + t];
+    int kk = 0;
+    while (!(kk < sd.nb && kk != sd.pos && t >= first[kk] && t < first[kk] + sd.dims[kk])) ++kk;
+    const int dd = t - first[kk];
+    const double l2 = lam[sd.bond[kk] * chi + dd];
+    if (l2 > 0.0) lambar[sd.bond[kk] * chi + dd] += sign * tot / l2;
+  }
+  __syncthreads();
 }
-
 
 // Strides of a final site's tensor per direction (left, right, down, up); 0 if absent.
 __device__ void site_strides(const FinalSite& fs, int* stride) {
@@ -437,7 +470,8 @@ __device__ __forceinline__ int side_rows(const SideDesc& sd, int& lo0, int& hi0,
 // Adjoint of gate g (see the file comment).  gbar[site] holds the adjoint of the gate's
 // output tensors on entry and of its input tensors on exit; lam[bond] goes back to the
 // value before the gate; lambar[bond] becomes the adjoint of that value.
-__device__ void gate_bwd(const AdjArgs& a, int b, int g, double* scr, double* gbar, double* lambar, double* lam) {
+__device__ void gate_bwd(const AdjArgs& a, int b, int g, double* scr, double* gbar, double* lambar, double* lam,
+                         double* red) {
   const GateDesc& gd = a.gates[g];
   const int D = gd.D, chi = a.chi, bond = gd.bond, L2 = 2 * chi, CC = chi * chi;
   const double* rec = a.rec_core + ((int64_t)g * a.B + b) * core_rec_elems(chi);
@@ -460,38 +494,49 @@ __device__ void gate_bwd(const AdjArgs& a, int b, int g, double* scr, double* gb
   auto cval = [&](int ka, int kb) { return ka == kb ? 0.5 : cpm; };
   const double* hist = a.hist + (int64_t)b * a.hist_elems;
   // (a) X-bar = G_new-bar / env, environment adjoints of G_new = X / env; (b) C = M'^T X-bar
+  double* rq = scr + a.o_xbar + 2 * a.max_site;   // per-(row, column) partial sums (see prepare_reverse)
   for (int X = 0; X < 2; ++X) {
     const SideDesc& sd = gd.side[X];
     const int OI = sd.outer * sd.inner, Dn = gd.Dn;
     const double* Gn = hist + sd.out_off;
     const double* Gnb = gbar + (int64_t)sd.site * a.max_site;
     double* xb = scr + a.o_xbar + (int64_t)X * a.max_site;
-    for (int oi = threadIdx.x; oi < OI; oi += blockDim.x) {
+    for (int w = threadIdx.x; w < OI * Dn; w += blockDim.x) {
       int dig[kMaxBonds];
+      const int oi = w / Dn, j = w % Dn;
       const int o = oi / sd.inner, i = oi % sd.inner;
-      const double w = env_weight(sd, o, i, lam, chi, dig);
-      cs.wrow[oi] = w;
-      const double winv = w > 0.0 ? 1.0 / w : 0.0;
+      const double wt = env_weight(sd, o, i, lam, chi, dig);
+      if (j == 0) cs.wrow[oi] = wt;
+      const double winv = wt > 0.0 ? 1.0 / wt : 0.0;
       double r = 0.0;
-      for (int ph = 0; ph < sd.P; ++ph)
-        for (int j = 0; j < Dn; ++j) {
-          const int64_t e = (((int64_t)ph * sd.outer + o) * Dn + j) * sd.inner + i;
-          r += Gnb[e] * Gn[e];
-          xb[e] = (j < k) ? Gnb[e] * winv : 0.0;
-        }
+      for (int ph = 0; ph < sd.P; ++ph) {
+        const int64_t e = (((int64_t)ph * sd.outer + o) * Dn + j) * sd.inner + i;
+        r += Gnb[e] * Gn[e];
+        xb[e] = (j < k) ? Gnb[e] * winv : 0.0;
+      }
+      rq[w] = r;
+    }
+    bsync();
+    for (int oi = threadIdx.x; oi < OI; oi += blockDim.x) {
+      double r = 0.0;
+      for (int j = 0; j < Dn; ++j) r += rq[oi * Dn + j];
       rsum[oi] = r;
     }
     bsync();
-    env_lambar(sd, rsum, lam, lambar, chi, -1.0);
-    bsync();
+    env_lambar(sd, rsum, lam, lambar, chi, -1.0, red);
     int lo[2], hi[2];
     const int np = side_rows(sd, lo[0], hi[0], lo[1], hi[1]);
     const double* Gi = hist + sd.in_off;
-    for (int w = threadIdx.x; w < 2 * D * k; w += blockDim.x) {
-      const int kap = w / (D * k), q = (w / k) % D, j = w % k;
+    // C[kap][q][j]: tiles of 32 outputs; warp w takes rows w, w + nw, ...; lanes take outputs
+    const int NO = 2 * D * k, nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nrows = np * OI;
+    for (int o0 = 0; o0 < NO; o0 += 32) {
+      const int out = o0 + lane;
       double acc = 0.0;
-      for (int pr = 0; pr < np; ++pr)
-        for (int oi = 0; oi < OI; ++oi) {
+      if (out < NO) {
+        const int kap = out / (D * k), q = (out / k) % D, j = out % k;
+        for (int row = warp; row < nrows; row += nw) {
+          const int pr = row / OI, oi = row % OI;
           const int o = oi / sd.inner, i = oi % sd.inner;
           const double gl = Gi[(((int64_t)lo[pr] * sd.outer + o) * D + q) * sd.inner + i];
           const double gh = Gi[(((int64_t)hi[pr] * sd.outer + o) * D + q) * sd.inner + i];
@@ -499,9 +544,17 @@ __device__ void gate_bwd(const AdjArgs& a, int b, int g, double* scr, double* gb
           const double xh = xb[(((int64_t)hi[pr] * sd.outer + o) * Dn + j) * sd.inner + i];
           acc += cs.wrow[oi] * (kap == 0 ? (gl + gh) * (xl + xh) : (gl - gh) * (xl - xh));
         }
-      cs.C[X][(kap * D + q) * chi + j] = acc * kRs2;  // M'_lo = (Y, Z) / sqrt2, M'_hi = (Y, -Z) / sqrt2
+      }
+      red[threadIdx.x] = acc;
+      bsync();
+      if (warp == 0 && out < NO) {
+        double tot = 0.0;
+        for (int ww = 0; ww < nw; ++ww) tot += red[ww * 32 + lane];
+        const int kap = out / (D * k), q = (out / k) % D, j = out % k;
+        cs.C[X][(kap * D + q) * chi + j] = tot * kRs2;   // M'_lo = (Y, Z) / sqrt2, M'_hi = (Y, -Z) / sqrt2
+      }
+      bsync();
     }
-    bsync();
   }
   // (c) adjoint of the core theta = R_A Lambda' R_B^T (rA x rB) from its recorded SVD
   int rr = 0;
@@ -661,7 +714,8 @@ __device__ void gate_bwd(const AdjArgs& a, int b, int g, double* scr, double* gb
   }
   bsync();
   // (d) row update: M'-bar = M' Mx + X-bar Xx, back through the kappa basis, the doubling
-  // and the environment weights; G_in-bar into gbar[site]
+  // and the environment weights; G_in-bar into gbar[site].  One thread per (row, q): the
+  // columns (+, q) and (-, q) of the lo and hi rows.
   for (int X = 0; X < 2; ++X) {
     const SideDesc& sd = gd.side[X];
     const int OI = sd.outer * sd.inner, Dn = gd.Dn;
@@ -672,48 +726,53 @@ __device__ void gate_bwd(const AdjArgs& a, int b, int g, double* scr, double* gb
     double* gout = gbar + (int64_t)sd.site * a.max_site;
     const double* Mx = cs.Mx[X];
     const double* Xx = cs.Xx[X];
-    for (int oi = threadIdx.x; oi < OI; oi += blockDim.x) {
+    for (int w = threadIdx.x; w < OI * D; w += blockDim.x) {
       int dig[kMaxBonds];
+      const int oi = w / D, q = w % D;
       const int o = oi / sd.inner, i = oi % sd.inner;
-      const double w = env_weight(sd, o, i, lam, chi, dig);
+      const double wt = env_weight(sd, o, i, lam, chi, dig);
       double r = 0.0;
       for (int pr = 0; pr < np; ++pr) {
-        double ml[2 * kMaxChi], mh[2 * kMaxChi];
-        for (int q = 0; q < D; ++q) {
-          const double gl = Gi[(((int64_t)lo[pr] * sd.outer + o) * D + q) * sd.inner + i];
-          const double gh = Gi[(((int64_t)hi[pr] * sd.outer + o) * D + q) * sd.inner + i];
-          ml[q] = w * (gl + gh) * kRs2;
-          ml[D + q] = w * (gl - gh) * kRs2;
+        const int64_t bl = ((int64_t)lo[pr] * sd.outer + o) * D * sd.inner + i;
+        const int64_t bh = ((int64_t)hi[pr] * sd.outer + o) * D * sd.inner + i;
+        double lp = 0.0, hp = 0.0, lm = 0.0, hm = 0.0;   // M'-bar lo/hi at columns (+, q), (-, q)
+        for (int c = 0; c < D; ++c) {
+          const double gl = Gi[bl + (int64_t)c * sd.inner], gh = Gi[bh + (int64_t)c * sd.inner];
+          const double y = wt * (gl + gh) * kRs2, z = wt * (gl - gh) * kRs2;
+          const double mpp = Mx[c * L2 + q], mpm = Mx[c * L2 + D + q];
+          const double mmp = Mx[(D + c) * L2 + q], mmm = Mx[(D + c) * L2 + D + q];
+          lp += y * mpp + z * mmp;
+          hp += y * mpp - z * mmp;
+          lm += y * mpm + z * mmm;
+          hm += y * mpm - z * mmm;
         }
-        double bl[2 * kMaxChi], bh[2 * kMaxChi];
-        for (int col = 0; col < 2 * D; ++col) {
-          double al = 0.0, ah = 0.0;
-          for (int c = 0; c < D; ++c) {
-            al += ml[c] * Mx[c * L2 + col] + ml[D + c] * Mx[(D + c) * L2 + col];
-            ah += ml[c] * Mx[c * L2 + col] - ml[D + c] * Mx[(D + c) * L2 + col];
-          }
-          for (int j = 0; j < k; ++j) {
-            al += xb[(((int64_t)lo[pr] * sd.outer + o) * Dn + j) * sd.inner + i] * Xx[j * L2 + col];
-            ah += xb[(((int64_t)hi[pr] * sd.outer + o) * Dn + j) * sd.inner + i] * Xx[j * L2 + col];
-          }
-          bl[col] = al;
-          bh[col] = ah;
+        const int64_t xl0 = ((int64_t)lo[pr] * sd.outer + o) * Dn * sd.inner + i;
+        const int64_t xh0 = ((int64_t)hi[pr] * sd.outer + o) * Dn * sd.inner + i;
+        for (int j = 0; j < k; ++j) {
+          const double xl = xb[xl0 + (int64_t)j * sd.inner], xh = xb[xh0 + (int64_t)j * sd.inner];
+          const double xp = Xx[j * L2 + q], xm = Xx[j * L2 + D + q];
+          lp += xl * xp;
+          hp += xh * xp;
+          lm += xl * xm;
+          hm += xh * xm;
         }
-        for (int q = 0; q < D; ++q) {
-          const double yb = (bl[q] + bh[q]) * kRs2, zb = (bl[D + q] - bh[D + q]) * kRs2;
-          const double gbl = yb + zb, gbh = yb - zb;   // adjoints of the weighted lo / hi entries
-          const int64_t el = (((int64_t)lo[pr] * sd.outer + o) * D + q) * sd.inner + i;
-          const int64_t eh = (((int64_t)hi[pr] * sd.outer + o) * D + q) * sd.inner + i;
-          r += gbl * w * Gi[el] + gbh * w * Gi[eh];
-          gout[el] = gbl * w;
-          gout[eh] = gbh * w;
-        }
+        const double yb = (lp + hp) * kRs2, zb = (lm - hm) * kRs2;
+        const double gbl = yb + zb, gbh = yb - zb;   // adjoints of the weighted lo / hi entries
+        const int64_t el = bl + (int64_t)q * sd.inner, eh = bh + (int64_t)q * sd.inner;
+        r += gbl * wt * Gi[el] + gbh * wt * Gi[eh];
+        gout[el] = gbl * wt;
+        gout[eh] = gbh * wt;
       }
+      rq[w] = r;
+    }
+    bsync();
+    for (int oi = threadIdx.x; oi < OI; oi += blockDim.x) {
+      double r = 0.0;
+      for (int q = 0; q < D; ++q) r += rq[oi * D + q];
       rsum[oi] = r;
     }
     bsync();
-    env_lambar(sd, rsum, lam, lambar, chi, 1.0);
-    bsync();
+    env_lambar(sd, rsum, lam, lambar, chi, 1.0, red);
   }
   // the bond's weight and its adjoint go back to before the gate
   for (int q = threadIdx.x; q < chi; q += blockDim.x) {
@@ -760,6 +819,7 @@ __device__ void local_bwd(const AdjArgs& a, int b, int t, int s, double* gbar, d
 
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a) {
   __shared__ double red[33];
+  __shared__ double red2[256];
   const int b = blockIdx.x;
   double* scr = a.scratch + (int64_t)b * a.scr_stride;
   double* gbar = scr + a.o_gbar;
@@ -779,7 +839,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a) {
   __syncthreads();
   for (int t = a.T - 1; t >= 0; --t) {
     for (int rd = a.layer_round[t + 1] - 1; rd >= a.layer_round[t]; --rd)
-      for (int g = a.round_first[rd + 1] - 1; g >= a.round_first[rd]; --g) gate_bwd(a, b, g, scr, gbar, lambar, lam);
+      for (int g = a.round_first[rd + 1] - 1; g >= a.round_first[rd]; --g) gate_bwd(a, b, g, scr, gbar, lambar, lam, red2);
     for (int s = 0; s < a.S; ++s) local_bwd(a, b, t, s, gbar, red);
   }
 }

@@ -639,7 +639,7 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
   A = td::AdjArgs{};
   A.max_site = max_site;
   A.o_gbar = take(max_site * P.S);
-  A.o_xbar = take(2 * max_site);
+  A.o_xbar = take(3 * max_site);   // two sides' X-bar, then per-(row, column) partial sums
   A.o_r = take(max_site);
   A.o_lambar = take((int64_t)P.n_bonds * chi);
   A.o_core = take(td::CoreScr_elems(chi, max_site));
