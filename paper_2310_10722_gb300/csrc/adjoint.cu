@@ -148,7 +148,8 @@ __device__ __forceinline__ double dir_weight(const FinalSite& fs, const double* 
 // Adjoint of the final contraction (the zip-up of final.cu): fills gbar[s] (adjoint of each
 // site's last tensor), adds to lambar (sqrt(lambda) on both sides of every bond) and writes
 // the readouts' adjoints.
-__device__ void final_bwd(const AdjArgs& a, int b, double* scr, double* gbar, double* lambar, double* Rbar) {
+__device__ void final_bwd(const AdjArgs& a, int b, double* scr, double* gbar, double* lambar, double* Rbar,
+                          double* red, double* red2) {
   const int nx = a.nx, ny = a.ny, chi = a.chi;
   const double* rec = a.rec_fin + (int64_t)b * a.fin_stride;
   const FinRecSlot ly(a.fin_mC, a.fin_mA, a.fin_m, a.fin_n);
@@ -166,6 +167,9 @@ __device__ void final_bwd(const AdjArgs& a, int b, double* scr, double* gbar, do
   double* Ub = scr + a.fo_Ub;
   double* W = scr + a.fo_W;
   double* J = scr + a.fo_J;
+  double* In = scr + a.fo_In;     // F_ij (J_ij - J_ji) s_j of a cut
+  double* wg = scr + a.fo_wg;     // per entry of a site: weight, then F-bar . F
+  int* offs = reinterpret_cast<int*>(scr + a.fo_off);
   const int mA = a.mps_stride;
   const double z = a.Z[2 * b] + a.Z[2 * b + 1];
   for (int w = threadIdx.x; w < nx * mA; w += blockDim.x) Aout[w] = 0.0;
@@ -200,6 +204,8 @@ __device__ void final_bwd(const AdjArgs& a, int b, double* scr, double* gbar, do
           const int off = il * stride[0] + ir * stride[1] + id * stride[2] + iu * stride[3];
           const double wgt = dir_weight(fs, lam, chi, 0, il) * dir_weight(fs, lam, chi, 1, ir) *
                              dir_weight(fs, lam, chi, 2, id) * dir_weight(fs, lam, chi, 3, iu);
+          wg[e] = wgt;
+          offs[e] = off;
           double a0 = 0.0, a1 = 0.0;
           for (int ph = 0; ph < fs.P; ++ph) {
             const double gv = g[(int64_t)ph * nF + off];
@@ -283,36 +289,41 @@ __device__ void final_bwd(const AdjArgs& a, int b, double* scr, double* gbar, do
           J[w] = acc;
         }
         bsync();
-        // W[ju][j] (j < rr) = sum_i U_i[ju] F_ij (J_ij - J_ji) s_j + [j < k] (U-bar_j - sum_i U_i J_ij)[ju] / s_j
+        // In[i][j] = F_ij (J_ij - J_ji) s_j  (i, j < rr; J_ij = 0 for j >= k)
+        for (int w = threadIdx.x; w < rr * rr; w += blockDim.x) {
+          const int i = w / rr, j = w % rr;
+          double v = 0.0;
+          if (i != j && (i < k || j < k)) {
+            const double si = sv[(int)ordd[i]], sj = sv[(int)ordd[j]];
+            const double den = sj * sj - si * si;
+            const double Jij = (j < k) ? J[i * k + j] : 0.0;
+            const double Jji = (i < k) ? J[j * k + i] : 0.0;
+            if (den != 0.0) v = (Jij - Jji) / den * sj;
+          }
+          In[w] = v;
+        }
+        bsync();
+        // W[ju][j] = (sum_i U_i[ju] In[i][j] + [j < k] (U-bar_j - sum_i U_i J_ij)[ju] / s_j) / s_j
         for (int w = threadIdx.x; w < m * rr; w += blockDim.x) {
           const int ju = w / rr, j = w % rr;
-          const double sj = sv[(int)ordd[j]];
+          const double isj = 1.0 / sv[(int)ordd[j]];
           double acc = 0.0, proj = 0.0;
           for (int i = 0; i < rr; ++i) {
             const double ui = V[(int64_t)(int)ordd[i] * m + ju];
-            const double Jij = (j < k) ? J[i * k + j] : 0.0;
-            const double Jji = (i < k) ? J[j * k + i] : 0.0;
-            if (i != j) {
-              const double si = sv[(int)ordd[i]];
-              const double den = sj * sj - si * si;
-              if (den != 0.0) acc += ui * (Jij - Jji) / den * sj;
-            }
-            proj += ui * Jij;
+            acc += ui * In[i * rr + j];
+            if (j < k) proj += ui * J[i * k + j];
           }
-          if (j < k) acc += (Ub[ju * k + j] - proj) / sj;
-          W[w] = acc;
+          if (j < k) acc += (Ub[ju * k + j] - proj) * isj;
+          W[w] = acc * isj;
         }
         bsync();
-        // M-bar = inv0 V_k C-bar + W (MT_j / s_j)^T
+        // M-bar = inv0 V_k C-bar + W MT^T  (MT_j = s_j times the right singular vector)
         for (int w = threadIdx.x; w < m * n; w += blockDim.x) {
           const int ju = w / n, c = w % n;
           double acc = 0.0;
           for (int kk = 0; kk < k; ++kk) acc += V[(int64_t)(int)ordd[kk] * m + ju] * Cbar[kk * n + c];
           acc *= inv0;
-          for (int j = 0; j < rr; ++j) {
-            const int cj = (int)ordd[j];
-            acc += W[ju * rr + j] * MT[(int64_t)cj * n + c] / sv[cj];
-          }
+          for (int j = 0; j < rr; ++j) acc += W[ju * rr + j] * MT[(int64_t)(int)ordd[j] * n + c];
           Mb[w] = acc;
         }
       }
@@ -380,52 +391,52 @@ __device__ void final_bwd(const AdjArgs& a, int b, double* scr, double* gbar, do
       if (s >= 0) {
         const FinalSite& fs = a.finals[s];
         double* gb = gbar + (int64_t)s * a.max_site;
+        double rp[2 * kMaxPhys];
+        for (int w = 0; w < 2 * kMaxPhys; ++w) rp[w] = 0.0;
         for (int e = threadIdx.x; e < nF; e += blockDim.x) {
-          int q = e;
-          const int iu = q % U; q /= U;
-          const int id = q % aD; q /= aD;
-          const int ir = q % Rr; q /= Rr;
-          const int il = q;
-          const int off = il * stride[0] + ir * stride[1] + id * stride[2] + iu * stride[3];
-          const double wgt = dir_weight(fs, lam, chi, 0, il) * dir_weight(fs, lam, chi, 1, ir) *
-                             dir_weight(fs, lam, chi, 2, id) * dir_weight(fs, lam, chi, 3, iu);
-          for (int ph = 0; ph < fs.P; ++ph)
+          const double wgt = wg[e];
+          const int off = offs[e];
+          for (int ph = 0; ph < fs.P; ++ph) {
             gb[(int64_t)ph * nF + off] = (fs.R[ph * 2] * Fb[e] + fs.R[ph * 2 + 1] * Fb[nF + e]) * wgt;
-        }
-        for (int w = threadIdx.x; w < fs.P * 2; w += blockDim.x) {
-          const int ph = w / 2, c = w % 2;
-          double acc = 0.0;
-          for (int e = 0; e < nF; ++e) {
-            int q = e;
-            const int iu = q % U; q /= U;
-            const int id = q % aD; q /= aD;
-            const int ir = q % Rr; q /= Rr;
-            const int il = q;
-            const int off = il * stride[0] + ir * stride[1] + id * stride[2] + iu * stride[3];
-            const double wgt = dir_weight(fs, lam, chi, 0, il) * dir_weight(fs, lam, chi, 1, ir) *
-                               dir_weight(fs, lam, chi, 2, id) * dir_weight(fs, lam, chi, 3, iu);
-            acc += Fb[c * nF + e] * wgt * g[(int64_t)ph * nF + off];
+            const double gv = g[(int64_t)ph * nF + off] * wgt;
+            rp[ph * 2] += Fb[e] * gv;
+            rp[ph * 2 + 1] += Fb[nF + e] * gv;
           }
-          Rbar[(int64_t)s * 8 + w] = acc;
         }
-        for (int w = threadIdx.x; w < 4 * chi; w += blockDim.x) {
-          const int dir = w / chi, idx = w % chi;
-          if (fs.dir_pos[dir] < 0 || idx >= fs.dir_dim[dir]) continue;
-          const double l2 = lam[fs.dir_bond[dir] * chi + idx];
-          if (!(l2 > 0.0)) continue;
+        for (int w = 0; w < fs.P * 2; ++w) {
+          const double tot = block_sum(rp[w], red);
+          if (threadIdx.x == 0) Rbar[(int64_t)s * 8 + w] = tot;
+        }
+        // lambda-bar: sqrt(lambda) on each leg; entries of digit d of direction dir are
+        // e = h * (dim * st) + d * st + l in the [l][r][d][u] order
+        for (int e = threadIdx.x; e < nF; e += blockDim.x) wg[e] = Fb[e] * F[e] + Fb[nF + e] * F[nF + e];
+        bsync();
+        const int dims4[4] = {L, Rr, aD, U}, st4[4] = {Rr * aD * U, aD * U, U, 1};
+        int first[5], n_out = 0;
+        for (int dir = 0; dir < 4; ++dir) { first[dir] = n_out; if (fs.dir_pos[dir] >= 0) n_out += dims4[dir]; }
+        first[4] = n_out;
+        if (n_out > 0) {
+          const int parts = (int)blockDim.x / n_out, t = threadIdx.x;
           double acc = 0.0;
-          for (int e = 0; e < nF; ++e) {
-            int q = e;
-            const int iu = q % U; q /= U;
-            const int id = q % aD; q /= aD;
-            const int ir = q % Rr; q /= Rr;
-            const int il = q;
-            const int di[4] = {il, ir, id, iu};
-            if (di[dir] == idx) acc += Fb[e] * F[e] + Fb[nF + e] * F[nF + e];
+          if (t < parts * n_out) {
+            const int o = t % n_out, part = t / n_out;
+            int dir = 0;
+            while (!(fs.dir_pos[dir] >= 0 && o >= first[dir] && o < first[dir] + dims4[dir])) ++dir;
+            const int d = o - first[dir], dk = dims4[dir], sk = st4[dir], cnt = nF / dk;
+            for (int e = part; e < cnt; e += parts) acc += wg[(e / sk) * dk * sk + d * sk + e % sk];
           }
-          // at most one thread per (bond, index) and side; the two sides of a bond are
-          // different sites, handled at different (x, y): no concurrent update
-          lambar[fs.dir_bond[dir] * chi + idx] += acc / (2.0 * l2);
+          red2[t] = acc;
+          bsync();
+          if (t < n_out) {
+            double tot = 0.0;
+            for (int part = 0; part < parts; ++part) tot += red2[part * n_out + t];
+            int dir = 0;
+            while (!(fs.dir_pos[dir] >= 0 && t >= first[dir] && t < first[dir] + dims4[dir])) ++dir;
+            const int d = t - first[dir];
+            const double l2 = lam[fs.dir_bond[dir] * chi + d];
+            // the two sides of a bond are different sites, handled at different (x, y)
+            if (l2 > 0.0) lambar[fs.dir_bond[dir] * chi + d] += tot / (2.0 * l2);
+          }
         }
       }
       bsync();
@@ -835,7 +846,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a) {
   __syncthreads();
   const double z = a.Z[2 * b] + a.Z[2 * b + 1];
   if (!(z > 0.0) || !(z < INFINITY)) return;   // probability 0: contributes nothing
-  final_bwd(a, b, scr, gbar, lambar, Rb);
+  final_bwd(a, b, scr, gbar, lambar, Rb, red, red2);
   __syncthreads();
   for (int t = a.T - 1; t >= 0; --t) {
     for (int rd = a.layer_round[t + 1] - 1; rd >= a.layer_round[t]; --rd)

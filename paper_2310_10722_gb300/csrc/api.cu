@@ -650,6 +650,7 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
   A.fo_C0 = take(mMN); A.fo_C1 = take(mMN);
   A.fo_A0 = take(mA * P.nx); A.fo_A1 = take(mA * P.nx);
   A.fo_Ub = take((int64_t)m_max * cm); A.fo_W = take((int64_t)m_max * m_max); A.fo_J = take((int64_t)m_max * cm);
+  A.fo_In = take((int64_t)m_max * m_max); A.fo_wg = take(mF / 2); A.fo_off = take(mF / 4 + 1);
   A.scr_stride = acc;
   // FP64 final contraction of the recorded forward: work region in global scratch
   td::FinalArgs& G = net->gfin;

@@ -111,7 +111,8 @@ struct AdjArgs {
   int64_t scr_stride;
   int64_t o_gbar, o_xbar, o_r, o_lambar, o_core, o_fin;   // offsets in a shot's scratch
   int64_t max_site;            // elements per site slot of gbar
-  int64_t fo_F, fo_Fb, fo_T1, fo_T1b, fo_M, fo_Mb, fo_C0, fo_C1, fo_A0, fo_A1, fo_Ub, fo_W, fo_J;  // final scratch
+  int64_t fo_F, fo_Fb, fo_T1, fo_T1b, fo_M, fo_Mb, fo_C0, fo_C1, fo_A0, fo_A1, fo_Ub, fo_W, fo_J, fo_In, fo_wg,
+      fo_off;                  // final-contraction scratch
   int32_t S, T, nbonds, chi, nx, ny, B, n_gates, max_final_D, mps_stride;
   double* Kbar;                // [B][T * S][16]
   double* pbar;                // [B][n_gates]
