@@ -84,6 +84,52 @@ def cpu_baseline(chi, n_shots=CPU_SAMPLE, first=0):
                       f"{len(jobs)} spawned processes, wall {wall:.2f} s (CPU {sum(r[0] for r in res):.1f} s)"}
 
 
+_GRAD_JAC = {}
+
+
+def _oracle_grad_chunk(args):
+    first, n = args
+    from oracle import reverse
+    from td_inputs import log_uniform_rates, rotated_phenomenological, sample_shots
+    dem = log_uniform_rates(rotated_phenomenological(7, 7, 0.005, 0.005), seed=5000)
+    if "jac" not in _GRAD_JAC:       # the rates' map to the objects: once per worker, untimed
+        _GRAD_JAC["jac"] = reverse.object_jacobian(dem)
+    det, _ = sample_shots(dem, n, seed=5001, first_shot=first)
+    t = time.perf_counter()
+    reverse.reverse_grad_total_logprob(dem, det, 8, 8, jac=_GRAD_JAC["jac"])
+    return time.perf_counter() - t
+
+
+def cpu_grad_baseline(n_shots=16):
+    """Time the oracle's reverse sweep (numpy FP64) on the gradient workload, one shot per
+    process (spawn), after a warm-up call per worker."""
+    import multiprocessing as mp
+    cores = min(os.cpu_count() or 1, n_shots)
+    per = [n_shots // cores + (1 if i < n_shots % cores else 0) for i in range(cores)]
+    jobs, s = [], 0
+    for n in per:
+        if n:
+            jobs.append((s, n))
+            s += n
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    with ctx.Pool(len(jobs)) as pool:
+        pool.map(_oracle_grad_chunk, [(0, 1)] * len(jobs))
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_grad_chunk, jobs)
+        wall = time.perf_counter() - t0
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    return {"value": n_shots / wall, "unit": "gradient shots/s", "cores": len(jobs), "kind": "oracle",
+            "sample": f"{n_shots} shots of the gradient workload, oracle reverse sweep (numpy FP64, chi = 8), "
+                      f"{len(jobs)} spawned processes, wall {wall:.2f} s (CPU {sum(res):.1f} s)"}
+
+
 # ---------------------------------------------------------------- replicas
 def replica_first_shot(rank, shots_per_rank):
     """First shot of a rank's slice of the seeded stream: ranks decode disjoint, contiguous
@@ -429,6 +475,8 @@ def main():
                                       "decodes_per_shot": 1 + 2 * dem_g.n_mech,
                                       "max_abs_diff_vs_reverse_rel_to_max": float((gf - gr16).abs().max()
                                                                                   / gr16.abs().max())}
+        if rank == 0 and world == 1 and not args.no_cpu:
+            gres["cpu_baseline"] = cpu_grad_baseline()
         gres["note"] = (f"{g_shots} shots per GPU, chi = chi_mps = 8 (chi = 32 of the workload is out of reach: "
                         "~7 min per decode); reverse sweep in FP64: recorded forward + per-shot adjoint")
         ng.close()

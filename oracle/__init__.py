@@ -15,6 +15,11 @@ Contents (each function cites the passage of the paper it follows):
   pauli    -- the general optimal decoder of Sec. 2.3 over all 4^n Paulis.
   su       -- the approximate method of Sec. 4: sweep a PEPS through the layered network,
               simple-update truncation to chi after every gate, final boundary-MPS
-              contraction with chi_mps, then coset log-probabilities.
+              contraction with chi_mps, then coset log-probabilities; and the
+              gradient of its total log P by the affine identity in each rate.
+  reverse  -- the gradient of su's total log P by reverse-mode differentiation through
+              every step of the sweep, truncations included.
+  frozen   -- the "frozen projector" reading of the gradient, kept only to show that it
+              is not the gradient (tests/test_oracle_grad.py).
 All arithmetic is float64.  Pins are in tests/test_oracle_*.py.
 """

@@ -80,3 +80,32 @@ def test_frozen_projector_reading_is_rejected():
     lp, gf = frozen.frozen_grad(dem, det, 256, 1024)
     ge = exact.grad_total_logprob(dem, det)
     assert np.abs(gf - ge).max() > 0.1
+
+
+# ---- the reverse sweep of the oracle (oracle/reverse.py) --------------------------------------
+from oracle import reverse  # noqa: E402
+
+
+def test_reverse_sweep_untruncated_is_exact():
+    for dem in (rotated_phenomenological(3, 2, 0.05, 0.04), repetition_phenomenological(5, 3, 0.07, 0.03),
+                point_sector_3d(3, 0.05)):
+        det, _ = sample_shots(dem, 2, seed=11)
+        lp, g = reverse.reverse_grad_total_logprob(dem, det, chi=256, chi_mps=1024)
+        np.testing.assert_allclose(lp, exact.total_logprob(exact.transfer_matrix(dem, det)), rtol=1e-11, atol=1e-11)
+        np.testing.assert_allclose(g, exact.grad_total_logprob(dem, det), rtol=1e-10, atol=1e-10)
+
+
+def test_reverse_sweep_truncated_matches_differences():
+    """With truncation: central differences of su.su_logprob (step 1e-5 p_j)."""
+    dem = point_sector_3d(3, 0.08)
+    det, _ = sample_shots(dem, 2, seed=17)
+    lp, g = reverse.reverse_grad_total_logprob(dem, det, chi=2, chi_mps=8)
+    for j in range(0, dem.n_mech, 5):
+        h = 1e-5 * dem.p[j]
+        pp, pm = dem.p.copy(), dem.p.copy()
+        pp[j] += h
+        pm[j] -= h
+        a = su.su_logprob(dem.with_rates(pp), det, 2, 8)
+        b = su.su_logprob(dem.with_rates(pm), det, 2, 8)
+        fd = (np.logaddexp(a[:, 0], a[:, 1]) - np.logaddexp(b[:, 0], b[:, 1])) / (2 * h)
+        np.testing.assert_allclose(g[:, j], fd, rtol=1e-6, atol=1e-6)
