@@ -828,7 +828,7 @@ __device__ void local_bwd(const AdjArgs& a, int b, int t, int s, double* gbar, d
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_adjoint(AdjArgs a) {
+__global__ void __launch_bounds__(256, 4) k_adjoint(AdjArgs a) {
   __shared__ double red[33];
   __shared__ double red2[256];
   const int b = blockIdx.x;
