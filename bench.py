@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--chi", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU path")
     ap.add_argument("--shots", type=int, default=SHOTS, help="shots per GPU (profiling runs use fewer)")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (reported beside the line)")
@@ -285,6 +286,8 @@ def main():
     work = net.work()
     waves = math.ceil(SHOTS / info["wave"])
     stream = torch.cuda.current_stream()
+    # launch schedule picked by the autotuner on the first 1024 shots (outside the timed region)
+    schedule = net.tune(det[:1024]) if not args.no_tune else None
 
     for _ in range(args.warmup):
         net.decode(det)
@@ -331,6 +334,7 @@ def main():
     if not args.no_fp64:
         net64 = td.Network.from_dem(dem, chi=chi, chi_mps=chi, precision=td.TD_FP64, mem_budget=96 << 30,
                                   max_wave=SHOTS)
+        sched64 = net64.tune(det[:1024]) if not args.no_tune else None
         net64.decode(det[:256])
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -358,7 +362,7 @@ def main():
                 "max_dlogP_total": float(torch.where(torch.isinf(tot32) & torch.isinf(tot64),
                                                      torch.zeros_like(tot32), (tot32 - tot64).abs()).max()),
                 "decisions_differ": dec_diff,
-                "decisions_differ_where_margin_gt_1e-3": dec_diff_sure}
+                "decisions_differ_where_margin_gt_1e-3": dec_diff_sure, "schedule": sched64}
         net64.close()
 
     # other workloads of the same path, reported beside the headline (a few seconds each)
@@ -397,13 +401,14 @@ def main():
     if extra is not None:
         from td_inputs import point_sector_3d
         per, chi_u = 32, 16
-        nets_u, dets_u, outs_u = [], [], []
+        nets_u, dets_u, outs_u, sched_u = [], [], [], []
         for dcode in (5, 7, 9, 11):
             dem_u = point_sector_3d(dcode, 0.1)
             du, _ = sample_shots(dem_u, per, seed=4000 + dcode)
             nets_u.append(td.Network.from_dem(dem_u, chi=chi_u, chi_mps=8, precision=td.TD_FP32,
                                               mem_budget=16 << 30))
             dets_u.append(torch.from_numpy(du).cuda())
+            sched_u.append(nets_u[-1].tune(dets_u[-1]))     # per-(d, chi) schedule, outside the capture
             outs_u.append(torch.empty((per, 2), dtype=torch.float64, device="cuda"))
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -425,8 +430,9 @@ def main():
         extra["point_sector_uneven_d5_7_9_11_chi16_graph"] = {
             "value": 4 * per / (ga.elapsed_time(gb) / 1000.0), "unit": UNIT, "shots": 4 * per,
             "replay_matches_eager": all(torch.equal(a, b) for a, b in zip(ref_u, outs_u)),
-            "note": "p=0.1, chi=16, chi_mps=8, FP32 storage; one network per code size, all decode "
-                    "calls captured in one CUDA graph"}
+            "schedules": {f"d{dc}": sc for dc, sc in zip((5, 7, 9, 11), sched_u)},
+            "note": "p=0.1, chi=16, chi_mps=8, FP32 storage; one network per code size with its launch "
+                    "schedule picked by td_network_tune, all decode calls captured in one CUDA graph"}
         for n_u in nets_u:
             n_u.close()
 
@@ -526,7 +532,7 @@ def main():
                    "precision": "fp32", "wave": info["wave"], "workspace_gb": info["workspace_bytes"] / 1e9,
                    "l2": f"not flushed: per-step working set {info['workspace_bytes'] / 1e9:.1f} GB of site tensors "
                          "rewritten every step, far above the 129 MB L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "schedule": schedule},
         "wall_s_timed": wall,
         "fp64_path": fp64,
         "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,

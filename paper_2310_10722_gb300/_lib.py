@@ -14,7 +14,8 @@ STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NONLOCAL", 3: "TD_ER
                 5: "TD_ERR_TIMEOUT", 6: "TD_ERR_NUMERIC", 7: "TD_ERR_UNSUPPORTED"}
 
 EXPORTS = ["td_default_options", "td_build_network", "td_coset_logprob", "td_decode",
-           "td_coset_logprob_host", "td_grad_logprob", "td_grad_logprob_forced", "td_network_get_info", "td_debug_sweep",
+           "td_coset_logprob_host", "td_grad_logprob", "td_grad_logprob_forced", "td_network_set_schedule",
+           "td_network_tune", "td_network_get_info", "td_debug_sweep",
            "td_network_profile", "td_network_get_work", "td_coset_logprob_static", "td_free_network",
            "td_last_error"]
 
@@ -75,6 +76,10 @@ def load(path: str | None = None):
     lib.td_grad_logprob.restype = C.c_int
     lib.td_grad_logprob_forced.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
     lib.td_grad_logprob_forced.restype = C.c_int
+    lib.td_network_set_schedule.argtypes = [vp, C.c_int32, C.c_int32]
+    lib.td_network_set_schedule.restype = C.c_int
+    lib.td_network_tune.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
+    lib.td_network_tune.restype = C.c_int
     lib.td_network_get_info.argtypes = [vp, C.POINTER(td_network_info)]
     lib.td_network_get_info.restype = C.c_int
     lib.td_debug_sweep.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, vp, C.POINTER(C.c_int32), vp]

@@ -17,6 +17,10 @@
 namespace {
 thread_local std::string g_err;
 
+// Schedule candidates of td_network_tune: k_final block size and rows per Gram / update job.
+constexpr int kFinalThreads[] = {256, 512, 1024};
+constexpr int kChunkCandidates[] = {512, 1024, 2048, 4096};
+
 td_status fail(td_status s, const std::string& msg) {
   g_err = msg;
   return s;
@@ -46,6 +50,9 @@ struct td_network {
   double* d_logp_stage = nullptr;
   int32_t nslots = 0;
   td::FinalArgs fin{};
+  int64_t fscr_elems = 0;       // final-contraction scratch per shot (largest candidate layout)
+  int smem_optin = 0;
+  int32_t chunk_rows = td::kChunkRows;   // rows per Gram / update job
   size_t bytes = 0;
   int64_t launches_per_wave = 0;
   std::vector<void*> allocs;
@@ -149,6 +156,49 @@ struct td_network {
   }
 };
 
+// Final-contraction layout (work region offsets, shared or global memory) for a block of
+// `threads` threads (the Jacobi lane groups and leading dimensions depend on it).
+static void final_layout(td_network* net, int threads) {
+  const td::Plan& P = net->plan;
+  const int cm = P.chi_mps, Dm = P.max_final_D;
+  const int64_t cmx = std::max(cm, 2);
+  const int64_t mps_stride = ((int64_t)cm * Dm * cmx + 3) / 4 * 4;
+  const int64_t mF = 2LL * Dm * Dm * Dm * Dm;
+  net->fin.threads = threads;
+  int64_t mMT = 0, mV = 0;   // M^T (n x m) and V (m x m) with the bank-spreading leading dimensions
+  {
+    const int n_max = (int)(cmx * Dm * 2), m_max = cm * Dm;
+    for (int m = 1; m <= m_max; ++m) {
+      const int g = td::team_svd_group(threads, n_max, m);
+      mMT = std::max<int64_t>(mMT, (int64_t)m * td::bank_ld32(n_max, g));
+      mV = std::max<int64_t>(mV, (int64_t)m * td::bank_ld32(m, g));
+    }
+  }
+  const int64_t mW = std::max<int64_t>((int64_t)cm * Dm * 2 * Dm * cmx, mV);
+  const int64_t mC = (int64_t)cm * cmx * Dm * 2;
+  const int64_t mS = 2LL * cm * Dm;
+  const int64_t mOrd = ((int64_t)cm * Dm * 4 + net->elem - 1) / net->elem;
+  int64_t wacc = 0;
+  auto wtake = [&](int64_t n) { int64_t r = wacc; wacc += (n + 3) / 4 * 4; return r; };
+  net->fin.w_F = wtake(mF);
+  net->fin.w_W = wtake(mW);
+  net->fin.w_MT = wtake(mMT);
+  net->fin.w_C0 = wtake(mC);
+  net->fin.w_C1 = wtake(mC);
+  net->fin.w_s = wtake(mS);
+  net->fin.w_ord = wtake(mOrd);
+  net->fin.work_elems = wacc;
+  const size_t static_smem = 8 * 1024;   // k_final's own shared arrays
+  net->fin.use_smem = ((size_t)wacc * net->elem + static_smem <= (size_t)net->smem_optin) ? 1 : 0;
+  int64_t acc = 0;
+  auto take = [&](int64_t n) { int64_t r = acc; acc += (n + 3) / 4 * 4; return r; };
+  net->fin.off_mps0 = take(mps_stride * P.nx);
+  net->fin.off_mps1 = take(mps_stride * P.nx);
+  net->fin.mps_stride = mps_stride;
+  net->fin.off_work = net->fin.use_smem ? 0 : take(wacc);
+  net->fin.scratch_elems = acc;
+}
+
 extern "C" {
 
 void td_default_options(td_options* opt) {
@@ -196,60 +246,32 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
 
   // final-contraction scratch per shot (elements of the accumulation type): the boundary
   // MPS (two buffers) in global memory, and the work region of one block -- in shared
-  // memory when it fits, otherwise after the MPS in global memory
-  const int64_t cmx = std::max(cm, 2);
-  const int64_t mps_stride = ((int64_t)cm * Dm * cmx + 3) / 4 * 4;
-  const int64_t mF = 2LL * Dm * Dm * Dm * Dm;
-  // Block size of k_final: 512 threads once the widest cut has >= 128 columns (more lanes
-  // per column pair in the Jacobi steps: rotated d=9, chi=16, chi_mps=8 runs 1.9x faster),
-  // 256 below (no gain at 64 columns).
-  net->fin.threads = (int64_t)cm * Dm >= 128 ? 512 : 256;
-  // M^T (n x m) and V (m x m) with the bank-spreading leading dimensions of k_final
-  int64_t mMT = 0, mV = 0;
-  {
-    const int n_max = (int)(cmx * Dm * 2), m_max = cm * Dm;
-    for (int m = 1; m <= m_max; ++m) {
-      const int g = td::team_svd_group(net->fin.threads, n_max, m);
-      mMT = std::max<int64_t>(mMT, (int64_t)m * td::bank_ld32(n_max, g));
-      mV = std::max<int64_t>(mV, (int64_t)m * td::bank_ld32(m, g));
-    }
-  }
-  const int64_t mW = std::max<int64_t>((int64_t)cm * Dm * 2 * Dm * cmx, mV);
-  const int64_t mC = (int64_t)cm * cmx * Dm * 2;
-  const int64_t mS = 2LL * cm * Dm;
-  const int64_t mOrd = ((int64_t)cm * Dm * 4 + net->elem - 1) / net->elem;
-  int64_t wacc = 0;
-  auto wtake = [&](int64_t n) { int64_t r = wacc; wacc += (n + 3) / 4 * 4; return r; };
-  net->fin.w_F = wtake(mF);
-  net->fin.w_W = wtake(mW);
-  net->fin.w_MT = wtake(mMT);
-  net->fin.w_C0 = wtake(mC);
-  net->fin.w_C1 = wtake(mC);
-  net->fin.w_s = wtake(mS);
-  net->fin.w_ord = wtake(mOrd);
-  net->fin.work_elems = wacc;
-  int smem_optin = 0, dev = 0;
+  // memory when it fits, otherwise after the MPS in global memory.  Block size of k_final:
+  // 512 threads once the widest cut has >= 128 columns (more lanes per column pair in the
+  // Jacobi steps: rotated d=9, chi=16, chi_mps=8 runs 1.9x faster), 256 below (no gain at 64
+  // columns); td_network_tune may pick another of kFinalThreads.  The scratch is sized for
+  // the largest layout of all candidates.
+  int dev = 0;
+  net->smem_optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaDeviceGetAttribute(&net->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
     cudaGetLastError();
-    smem_optin = 0;
+    net->smem_optin = 0;
   }
-  const size_t static_smem = 8 * 1024;   // k_final's own shared arrays
-  net->fin.use_smem = ((size_t)wacc * net->elem + static_smem <= (size_t)smem_optin) ? 1 : 0;
   int64_t acc = 0;
-  auto take = [&](int64_t n) { int64_t r = acc; acc += (n + 3) / 4 * 4; return r; };
-  net->fin.off_mps0 = take(mps_stride * P.nx);
-  net->fin.off_mps1 = take(mps_stride * P.nx);
-  net->fin.mps_stride = mps_stride;
-  net->fin.off_work = net->fin.use_smem ? 0 : take(wacc);
-  net->fin.scratch_elems = acc;
+  for (int th : kFinalThreads) {
+    final_layout(net, th);
+    acc = std::max<int64_t>(acc, net->fin.scratch_elems);
+  }
+  final_layout(net, (int64_t)cm * Dm >= 128 ? 512 : 256);
+  net->fscr_elems = acc;
 
   int max_chunks = 1;
   for (const td::LayerPlan& L : P.layers)
-    for (const td::Round& rd : L.rounds) max_chunks = std::max(max_chunks, td::absorb_chunks(rd.max_rows, td::kChunkRows));
+    for (const td::Round& rd : L.rounds) max_chunks = std::max(max_chunks, td::absorb_chunks(rd.max_rows, td::kMinChunkRows));
   const size_t per_shot = P.shot_elems * net->elem + (size_t)P.n_bonds * chi * 8 + (size_t)net->nslots * 8 +
                           (size_t)P.max_round_gates * 4 * chi * chi * (8 * max_chunks + 8) +
-                          (size_t)acc * net->elem + 16 + (size_t)P.n_det + 16;
+                          (size_t)net->fscr_elems * net->elem + 16 + (size_t)P.n_det + 16;
   const size_t budget = o.mem_budget ? o.mem_budget : (size_t(16) << 30);
   int64_t wave = (int64_t)(budget / std::max<size_t>(per_shot, 1));
   if (o.max_wave > 0) wave = std::min<int64_t>(wave, o.max_wave);
@@ -262,7 +284,7 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
             net->alloc(net->d_logacc, (size_t)wave * net->nslots * 8) &&
             net->alloc(net->d_gram, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * 8 * max_chunks) &&
             net->alloc(net->d_tbuf, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * 8) &&
-            net->alloc(net->d_fscr, (size_t)wave * acc * net->elem) &&
+            net->alloc(net->d_fscr, (size_t)wave * net->fscr_elems * net->elem) &&
             net->alloc(net->d_Z, (size_t)wave * 2 * 8) &&
             net->alloc(net->d_gates, sizeof(td::GateDesc) * P.gates.size()) &&
             net->alloc(net->d_locals, sizeof(td::LocalDesc) * P.locals.size()) &&
@@ -322,6 +344,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     a.multiplet_rtol = P.multiplet_rtol;
     a.vs = vs;
     a.ovr = ovr;
+    a.chunk_rows = net->chunk_rows;
     const bool f64 = P.precision == TD_FP64;
     cudaError_t e;
     {
@@ -768,6 +791,7 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
     a.B = Bw;
     a.gram_cutoff = P.gram_cutoff; a.svd_cutoff = P.svd_cutoff; a.multiplet_rtol = P.multiplet_rtol;
     a.rec_core = net->d_rec_core;
+    a.chunk_rows = net->chunk_rows;
     if ((e = td::launch_sweep_init<double, double>(a, net->d_hlocals, S, st)) != cudaSuccess) return cuda_fail(e, "init launch");
     for (int32_t t = 0; t < T; ++t) {
       a.layer = t;
@@ -847,6 +871,76 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "gradient copy");
   }
+  return TD_OK;
+}
+
+// ---- schedule -------------------------------------------------------------------------------
+td_status td_network_set_schedule(td_network* net, int32_t final_threads, int32_t chunk_rows) {
+  g_err.clear();
+  if (!net) return fail(TD_ERR_INVALID, "null network");
+  bool ok_t = false, ok_c = false;
+  for (int th : kFinalThreads) ok_t |= (th == final_threads);
+  for (int c : kChunkCandidates) ok_c |= (c == chunk_rows);
+  if (!ok_t) return fail(TD_ERR_INVALID, "final_threads must be 256, 512 or 1024");
+  if (!ok_c) return fail(TD_ERR_INVALID, "chunk_rows must be 512, 1024, 2048 or 4096");
+  final_layout(net, final_threads);
+  net->chunk_rows = chunk_rows;
+  return TD_OK;
+}
+
+td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, int32_t* final_threads,
+                          int32_t* chunk_rows, double* ms_best, void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (B < 1) return fail(TD_ERR_INVALID, "tuning needs at least one shot");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t Bs = std::min<int64_t>(B, net->wave);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "event create");
+  }
+  auto time_one = [&](float& ms) -> td_status {
+    td_status r = run(net, det_dev, Bs, net->d_logp_stage, nullptr, nullptr, st);   // warm-up
+    if (r != TD_OK) return r;
+    cudaEventRecord(e0, st);
+    r = run(net, det_dev, Bs, net->d_logp_stage, nullptr, nullptr, st);
+    if (r != TD_OK) return r;
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    return e == cudaSuccess ? TD_OK : cuda_fail(e, "tuning timing");
+  };
+  // coordinate descent: the final contraction's block size at the current chunk size, then
+  // the chunk size at the best block size
+  int best_t = net->fin.threads, best_c = net->chunk_rows;
+  float best = 0.0f;
+  s = time_one(best);
+  for (int th : kFinalThreads) {
+    if (s != TD_OK) break;
+    if (th == best_t) continue;
+    final_layout(net, th);
+    float ms = 0.0f;
+    s = time_one(ms);
+    if (s == TD_OK && ms < best) { best = ms; best_t = th; }
+  }
+  final_layout(net, best_t);
+  for (int c : kChunkCandidates) {
+    if (s != TD_OK) break;
+    if (c == best_c) continue;
+    net->chunk_rows = c;
+    float ms = 0.0f;
+    s = time_one(ms);
+    if (s == TD_OK && ms < best) { best = ms; best_c = c; }
+  }
+  net->chunk_rows = best_c;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != TD_OK) return s;
+  if (final_threads) *final_threads = best_t;
+  if (chunk_rows) *chunk_rows = best_c;
+  if (ms_best) *ms_best = best;
   return TD_OK;
 }
 

@@ -77,7 +77,7 @@ __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y
 // shared memory when it fits, otherwise in the shot's global scratch; the boundary MPS is
 // always in global scratch.
 template <typename R>
-__global__ void k_final(FinalArgs fa) {
+__global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
   const int b = blockIdx.x;
   const Team tm{(int)threadIdx.x, (int)blockDim.x, 1};
   extern __shared__ __align__(16) unsigned char smem_raw[];

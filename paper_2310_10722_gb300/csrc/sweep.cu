@@ -119,12 +119,13 @@ cudaError_t launch_round(const SweepArgs& a0, const GateDesc* gates, const Round
   const GateDesc* g = gates + rd.first;
   const int D = std::max(rd.maxD, rd.maxDn);
   SweepArgs a = a0;
-  a.gram_chunks = absorb_chunks(rd.max_rows, kChunkRows);
+  const int cr = a0.chunk_rows > 0 ? a0.chunk_rows : kChunkRows;
+  a.gram_chunks = absorb_chunks(rd.max_rows, cr);
   a.gate_base = rd.first;
   auto B = [&](int k) { if (prof) prof->begin(k); };
   auto E = [&](int k) { if (prof) prof->end(k); };
   B(TD_K_GRAM);
-  cudaError_t e = launch_gram2<T>(a, g, rd.count, D, gram, a.gram_chunks, kChunkRows, st);
+  cudaError_t e = launch_gram2<T>(a, g, rd.count, D, gram, a.gram_chunks, cr, st);
   E(TD_K_GRAM);
   if (e != cudaSuccess) return e;
   B(TD_K_CORE);
@@ -132,7 +133,7 @@ cudaError_t launch_round(const SweepArgs& a0, const GateDesc* gates, const Round
   E(TD_K_CORE);
   if (e != cudaSuccess) return e;
   B(TD_K_UPDATE);
-  e = launch_update2<T>(a, g, rd.count, D, tbuf, a.gram_chunks, kChunkRows, st);
+  e = launch_update2<T>(a, g, rd.count, D, tbuf, a.gram_chunks, cr, st);
   E(TD_K_UPDATE);
   return e;
 }

@@ -18,6 +18,7 @@ struct SweepArgs {
   int32_t wave_first;       // first shot of this wave in `det`
   int32_t B;                // shots in this wave
   int32_t gram_chunks;      // partial Grams per (gate, shot) of the current round (row chunks)
+  int32_t chunk_rows;       // rows per Gram / update job (0: kChunkRows)
   double gram_cutoff, svd_cutoff, multiplet_rtol;
   // gradient pass (null otherwise): virtual shots [*] and their override table
   const VShot* vs;
@@ -168,7 +169,8 @@ size_t core2_smem_bytes(int Dm);
 
 // Gram and update passes (absorb.cu), one warp per (gate side, shot, chunk of kChunkRows
 // rows); Dm = the round's largest bond dimension (before or after the gate).
-constexpr int kChunkRows = 2048;
+constexpr int kChunkRows = 2048;      // default
+constexpr int kMinChunkRows = 512;    // smallest schedule candidate (sizes the partial-Gram buffer)
 int absorb_chunks(int max_rows, int chunk_rows);
 template <typename T>
 cudaError_t launch_gram2(const SweepArgs& a, const GateDesc* g, int count, int Dm, double* gram, int nchunk,
