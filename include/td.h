@@ -83,7 +83,8 @@ typedef struct {
   int32_t chi;             /* simple-update bond cap (Sec. 4; chi_SU of Sec. 5) */
   int32_t chi_mps;         /* final boundary-MPS bond cap (chi_MPS of Sec. 5) */
   int32_t precision;       /* td_precision */
-  int32_t ckpt_stride;     /* reserved for the adjoint sweep (layers between checkpoints) */
+  int32_t ckpt_stride;     /* unused: td_grad_logprob keeps every intermediate site tensor of
+                              the sweep (versioned layout) instead of checkpoints every k layers */
   double svd_cutoff;       /* keep singular values s_i > svd_cutoff * s_1 */
   double multiplet_rtol;   /* a cut inside s_k - s_{k+1} <= rtol * s_1 drops the multiplet */
   double gram_cutoff;      /* drop Gram eigen-directions below gram_cutoff * max eigenvalue;

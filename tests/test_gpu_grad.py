@@ -153,3 +153,18 @@ def test_grad_waves_and_fp32_network(td):
     _, f64, _ = _grad(td, dem, det, method="forced", chi=8, chi_mps=16, precision=td.TD_FP64)
     _, f32, _ = _grad(td, dem, det, method="forced", chi=8, chi_mps=16, precision=td.TD_FP32)
     assert _rel(f32, f64) < 1e-3, _rel(f32, f64)
+
+
+def test_grad_full_size_sampled(td):
+    """The differentiation workload's network (rotated d=7, 7+1 rounds, 560 log-uniform
+    rates) at chi = chi_mps = 8, the launch configuration bench.py times: the reverse sweep of
+    single shots against the oracle's reverse sweep of the same shots."""
+    from oracle import reverse
+    dem = log_uniform_rates(rotated_phenomenological(7, 7, 0.005, 0.005), seed=5000)
+    det, _ = sample_shots(dem, 2, seed=5001)
+    jac = reverse.object_jacobian(dem)
+    for b in range(2):
+        logP, g, _ = _grad(td, dem, det[b:b + 1], chi=8, chi_mps=8)
+        lp_ref, g_ref = reverse.reverse_grad_total_logprob(dem, det[b:b + 1], 8, 8, jac=jac)
+        assert abs(logP[0] - lp_ref[0]) < 1e-6
+        assert _rel(g, g_ref[0]) < 1e-5, _rel(g, g_ref[0])
