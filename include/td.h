@@ -199,20 +199,23 @@ td_status td_grad_logprob_forced(td_network* net, const uint8_t* det_dev, int64_
 
 /* Launch schedule of the network (a property of this library; the paper has none): the
  * block size of the final contraction's kernel (256, 512 or 1024 threads; the Jacobi lane
- * groups and the work region's layout follow it) and the rows per job of the Gram and update
- * passes (512, 1024, 2048 or 4096).  Results do not depend on the schedule beyond rounding
- * (the Gram's partial sums and the Jacobi rotations are grouped differently).
+ * groups and the work region's layout follow it), whether that kernel's work region may sit
+ * in shared memory (final_smem != 0: when it fits; 0: global memory, cached in L1, which
+ * leaves room for more blocks per SM), and the rows per job of the Gram and update passes
+ * (512, 1024, 2048 or 4096).  Results do not depend on the schedule beyond rounding (the
+ * Gram's partial sums and the Jacobi rotations are grouped differently).
  * td_network_set_schedule sets it; TD_ERR_INVALID for other values. */
-td_status td_network_set_schedule(td_network* net, int32_t final_threads, int32_t chunk_rows);
+td_status td_network_set_schedule(td_network* net, int32_t final_threads, int32_t final_smem, int32_t chunk_rows);
 
 /* Autotuner: times decodes of the first min(B, wave) shots of det_dev (device uint8
- * [B][n_det]) under the schedule candidates -- the final contraction's block size at the
- * current chunk size, then the chunk size at the best block size (two decodes per candidate,
- * the second timed with CUDA events on `stream`) -- and keeps the fastest.  Writes the chosen
- * values and the best time (ms; each pointer may be NULL).  Synchronous.  Errors as
+ * [B][n_det]) under the schedule candidates -- the final contraction's block size and work-
+ * region placement at the current chunk size, then the chunk size at the best of those (two
+ * decodes per candidate, the second timed with CUDA events on `stream`) -- and keeps the
+ * fastest.  Writes the chosen values (final_smem: 1 if the work region is in shared memory)
+ * and the best time (ms); each pointer may be NULL.  Synchronous.  Errors as
  * td_coset_logprob; TD_ERR_INVALID for B < 1. */
 td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, int32_t* final_threads,
-                          int32_t* chunk_rows, double* ms_best, void* stream);
+                          int32_t* final_smem, int32_t* chunk_rows, double* ms_best, void* stream);
 
 td_status td_network_get_info(const td_network* net, td_network_info* info);
 

@@ -145,18 +145,19 @@ class Network:
                  C.c_void_p(grad.data_ptr()), self._stream(stream)))
         return logP, grad
 
-    def set_schedule(self, final_threads: int, chunk_rows: int):
-        """Launch schedule: k_final block size (256/512/1024), Gram/update rows per job."""
-        check(self._lib.td_network_set_schedule(self._h, int(final_threads), int(chunk_rows)))
+    def set_schedule(self, final_threads: int, chunk_rows: int, final_smem: bool = True):
+        """Launch schedule: k_final block size (256/512/1024) and work region in shared memory
+        (when it fits) or global memory, Gram/update rows per job (512..4096)."""
+        check(self._lib.td_network_set_schedule(self._h, int(final_threads), int(bool(final_smem)), int(chunk_rows)))
 
     def tune(self, det, stream=None) -> dict:
         """Autotune the launch schedule on decodes of det's first min(B, wave) shots; keeps
         and returns the fastest {final_threads, chunk_rows, ms}."""
         self._check_det(det)
-        th, cr, ms = C.c_int32(), C.c_int32(), C.c_double()
+        th, sm, cr, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
         check(self._lib.td_network_tune(self._h, C.c_void_p(det.data_ptr()), det.shape[0], C.byref(th),
-                                        C.byref(cr), C.byref(ms), self._stream(stream)))
-        return {"final_threads": th.value, "chunk_rows": cr.value, "ms": ms.value}
+                                        C.byref(sm), C.byref(cr), C.byref(ms), self._stream(stream)))
+        return {"final_threads": th.value, "final_smem": bool(sm.value), "chunk_rows": cr.value, "ms": ms.value}
 
     def debug_sweep(self, det, n_gates, stream=None):
         """Bond weights [B, n_bonds, chi] and log-scale slots after the first n_gates gates

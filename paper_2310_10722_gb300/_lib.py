@@ -76,9 +76,9 @@ def load(path: str | None = None):
     lib.td_grad_logprob.restype = C.c_int
     lib.td_grad_logprob_forced.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
     lib.td_grad_logprob_forced.restype = C.c_int
-    lib.td_network_set_schedule.argtypes = [vp, C.c_int32, C.c_int32]
+    lib.td_network_set_schedule.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
     lib.td_network_set_schedule.restype = C.c_int
-    lib.td_network_tune.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp]
+    lib.td_network_tune.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, vp]
     lib.td_network_tune.restype = C.c_int
     lib.td_network_get_info.argtypes = [vp, C.POINTER(td_network_info)]
     lib.td_network_get_info.restype = C.c_int

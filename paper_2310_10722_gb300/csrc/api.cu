@@ -158,7 +158,7 @@ struct td_network {
 
 // Final-contraction layout (work region offsets, shared or global memory) for a block of
 // `threads` threads (the Jacobi lane groups and leading dimensions depend on it).
-static void final_layout(td_network* net, int threads) {
+static void final_layout(td_network* net, int threads, bool allow_smem = true) {
   const td::Plan& P = net->plan;
   const int cm = P.chi_mps, Dm = P.max_final_D;
   const int64_t cmx = std::max(cm, 2);
@@ -189,7 +189,7 @@ static void final_layout(td_network* net, int threads) {
   net->fin.w_ord = wtake(mOrd);
   net->fin.work_elems = wacc;
   const size_t static_smem = 8 * 1024;   // k_final's own shared arrays
-  net->fin.use_smem = ((size_t)wacc * net->elem + static_smem <= (size_t)net->smem_optin) ? 1 : 0;
+  net->fin.use_smem = (allow_smem && (size_t)wacc * net->elem + static_smem <= (size_t)net->smem_optin) ? 1 : 0;
   int64_t acc = 0;
   auto take = [&](int64_t n) { int64_t r = acc; acc += (n + 3) / 4 * 4; return r; };
   net->fin.off_mps0 = take(mps_stride * P.nx);
@@ -259,10 +259,11 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
     net->smem_optin = 0;
   }
   int64_t acc = 0;
-  for (int th : kFinalThreads) {
-    final_layout(net, th);
-    acc = std::max<int64_t>(acc, net->fin.scratch_elems);
-  }
+  for (int th : kFinalThreads)
+    for (int sm = 0; sm < 2; ++sm) {
+      final_layout(net, th, sm == 1);
+      acc = std::max<int64_t>(acc, net->fin.scratch_elems);
+    }
   final_layout(net, (int64_t)cm * Dm >= 128 ? 512 : 256);
   net->fscr_elems = acc;
 
@@ -875,7 +876,7 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
 }
 
 // ---- schedule -------------------------------------------------------------------------------
-td_status td_network_set_schedule(td_network* net, int32_t final_threads, int32_t chunk_rows) {
+td_status td_network_set_schedule(td_network* net, int32_t final_threads, int32_t final_smem, int32_t chunk_rows) {
   g_err.clear();
   if (!net) return fail(TD_ERR_INVALID, "null network");
   bool ok_t = false, ok_c = false;
@@ -883,13 +884,13 @@ td_status td_network_set_schedule(td_network* net, int32_t final_threads, int32_
   for (int c : kChunkCandidates) ok_c |= (c == chunk_rows);
   if (!ok_t) return fail(TD_ERR_INVALID, "final_threads must be 256, 512 or 1024");
   if (!ok_c) return fail(TD_ERR_INVALID, "chunk_rows must be 512, 1024, 2048 or 4096");
-  final_layout(net, final_threads);
+  final_layout(net, final_threads, final_smem != 0);
   net->chunk_rows = chunk_rows;
   return TD_OK;
 }
 
 td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, int32_t* final_threads,
-                          int32_t* chunk_rows, double* ms_best, void* stream) {
+                          int32_t* final_smem, int32_t* chunk_rows, double* ms_best, void* stream) {
   g_err.clear();
   td_status s = check_call(net, det_dev, B);
   if (s != TD_OK) return s;
@@ -912,20 +913,22 @@ td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, in
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     return e == cudaSuccess ? TD_OK : cuda_fail(e, "tuning timing");
   };
-  // coordinate descent: the final contraction's block size at the current chunk size, then
-  // the chunk size at the best block size
-  int best_t = net->fin.threads, best_c = net->chunk_rows;
+  // coordinate descent: the final contraction's block size and work-region placement at the
+  // current chunk size, then the chunk size at the best of those
+  int best_t = net->fin.threads, best_sm = 1, best_c = net->chunk_rows;
+  final_layout(net, best_t, true);
   float best = 0.0f;
   s = time_one(best);
-  for (int th : kFinalThreads) {
-    if (s != TD_OK) break;
-    if (th == best_t) continue;
-    final_layout(net, th);
-    float ms = 0.0f;
-    s = time_one(ms);
-    if (s == TD_OK && ms < best) { best = ms; best_t = th; }
-  }
-  final_layout(net, best_t);
+  for (int th : kFinalThreads)
+    for (int sm = 1; sm >= 0; --sm) {
+      if (s != TD_OK) break;
+      if (th == best_t && sm == 1) continue;
+      final_layout(net, th, sm == 1);
+      float ms = 0.0f;
+      s = time_one(ms);
+      if (s == TD_OK && ms < best) { best = ms; best_t = th; best_sm = sm; }
+    }
+  final_layout(net, best_t, best_sm == 1);
   for (int c : kChunkCandidates) {
     if (s != TD_OK) break;
     if (c == best_c) continue;
@@ -939,6 +942,7 @@ td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, in
   cudaEventDestroy(e1);
   if (s != TD_OK) return s;
   if (final_threads) *final_threads = best_t;
+  if (final_smem) *final_smem = net->fin.use_smem;
   if (chunk_rows) *chunk_rows = best_c;
   if (ms_best) *ms_best = best;
   return TD_OK;

@@ -24,18 +24,19 @@ def td():
 
 @pytest.mark.parametrize("threads", [256, 512, 1024])
 @pytest.mark.parametrize("chunk", [512, 4096])
-def test_every_schedule_matches_the_oracle(td, threads, chunk):
+@pytest.mark.parametrize("smem", [True, False])
+def test_every_schedule_matches_the_oracle(td, threads, chunk, smem):
     import torch
     dem = point_sector_3d(3, 0.05)
     det, _ = sample_shots(dem, 64, seed=1000)
     net = td.Network.from_dem(dem, chi=8, chi_mps=64)
-    net.set_schedule(threads, chunk)
+    net.set_schedule(threads, chunk, smem)
     out = net.coset_logprob(torch.from_numpy(det).cuda()).cpu().numpy()
     assert np.abs(out - exact.transfer_matrix(dem, det)).max() < 1e-9
     dem5 = rotated_phenomenological(5, 4, 0.03, 0.03)
     det5, _ = sample_shots(dem5, 4, seed=7)
     net5 = td.Network.from_dem(dem5, chi=4, chi_mps=8)
-    net5.set_schedule(threads, chunk)
+    net5.set_schedule(threads, chunk, smem)
     out5 = net5.coset_logprob(torch.from_numpy(det5).cuda()).cpu().numpy()
     ref5 = su.su_logprob(dem5, det5, chi=4, chi_mps=8)
     assert np.abs(out5 - ref5).max() < 1e-6
