@@ -447,7 +447,8 @@ __device__ void final_bwd(const AdjArgs& a, int b, double* scr, double* gbar, do
   }
 }
 
-// Per-gate scratch of the core adjoint (doubles, L2 = 2 chi): see gate_bwd.
+// Per-gate scratch of the core adjoint (doubles, L2 = 2 chi; CoreScr_elems in sweep.cuh is its
+// size and must follow this carving): see gate_bwd.
 struct CoreScr {
   double *C[2], *Uq, *Vq, *Ub, *Vb, *J, *K, *In, *Th, *Tmp, *W1, *W2, *Mx[2], *Xx[2], *Lb, *wrow;
   __device__ CoreScr(double* base, int chi, int64_t max_oi) {
@@ -461,10 +462,7 @@ struct CoreScr {
     Mx[0] = take(L2 * L2); Mx[1] = take(L2 * L2); Xx[0] = take(chi * L2); Xx[1] = take(chi * L2);
     Lb = take(4 * chi); wrow = take(max_oi);
   }
-  static __host__ __device__ int64_t elems(int chi, int64_t max_oi) {
-    const int64_t L2 = 2 * chi;
-    return 2 * L2 * chi + 2 * L2 * L2 + 4 * L2 * chi + 5 * L2 * L2 + 2 * L2 * L2 + 2 * chi * L2 + 4 * chi + max_oi;
-  }
+  // total size: CoreScr_elems (sweep.cuh)
 };
 
 __device__ __forceinline__ int side_rows(const SideDesc& sd, int& lo0, int& hi0, int& lo1, int& hi1) {

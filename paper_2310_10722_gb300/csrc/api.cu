@@ -81,8 +81,7 @@ struct td_network {
   int32_t* d_layer_round = nullptr;
   int32_t grad_wave = 0;
   double *d_hist = nullptr, *d_rec_core = nullptr, *d_rec_sc = nullptr, *d_rec_fin = nullptr, *d_adj_scr = nullptr,
-         *d_gfscr = nullptr, *d_Kbar = nullptr, *d_pbar = nullptr, *d_Rbar = nullptr, *d_glogp = nullptr,
-         *d_grad_tmp = nullptr;
+         *d_gfscr = nullptr, *d_Kbar = nullptr, *d_pbar = nullptr, *d_Rbar = nullptr, *d_glogp = nullptr;
   td::AdjArgs adj{};
   td::FinalArgs gfin{};
   td_dem dem_view(const double* p) const {
