@@ -267,10 +267,7 @@ __device__ __forceinline__ int team_pow2_floor(int x) {
 // V (n x n, column-major, ldv) orthogonal -- so the singular values are the column norms
 // of A_out and its normalised columns the left singular vectors.  With init_V false, V
 // holds an orthogonal matrix on entry and is updated as V <- V J.  `flag` is one int of
-// team-shared scratch.  Sweeps stop after a sweep that rotated nothing, or after a sweep
-// whose rotations all had |a_p . a_q| <= 4 tol |a_p| |a_q| (the sweep that would follow only
-// confirms convergence: its pairs start within a few tol of orthogonal).  Returns the number
-// of sweeps.
+// team-shared scratch.  Returns the number of sweeps.
 // `tol`: convergence tolerance (<= 0: TeamTol<R>::rel()).
 template <typename R>
 __device__ int team_svd_onesided(const Team& tm, R* A, int lda, int m, int n, R* V, int ldv, int* flag,
@@ -317,8 +314,7 @@ __device__ int team_svd_onesided(const Team& tm, R* A, int lda, int m, int n, R*
         }
         R c, s;
         if (active && jacobi_rot(al, be, ga, tol, c, s)) {
-          // level 1: the pair was within 4 tol of orthogonal; level 2: further off
-          if (gl == 0) atomicMax(flag, (ga * ga <= R(16) * tol * tol * (al * be)) ? 1 : 2);
+          if (gl == 0) *flag = 1;
           for (int r = gl; r < m; r += g) {
             const R ap = ap_[r], aq = aq_[r];
             ap_[r] = c * ap - s * aq;
@@ -335,13 +331,9 @@ __device__ int team_svd_onesided(const Team& tm, R* A, int lda, int m, int n, R*
       }
       tm.sync();
     }
-    const int level = *flag;
+    const int any = *flag;
     tm.sync();
-    if (level == 0) break;
-    if (level == 1) {   // every rotation of this sweep was within 4 tol: no confirming sweep
-      ++sweep;
-      break;
-    }
+    if (!any) break;
   }
   return sweep;
 }
