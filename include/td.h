@@ -217,19 +217,6 @@ td_status td_network_set_schedule(td_network* net, int32_t final_threads, int32_
 td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, int32_t* final_threads,
                           int32_t* final_smem, int32_t* chunk_rows, double* ms_best, void* stream);
 
-/* Diagnostics of the truncations (a property of this library): with recording enabled,
- * td_coset_logprob and td_decode keep, for every shot of the call, the smallest relative
- * gap (s_{k-1} - s_k) / s_{k-1} between the last kept and the first dropped singular value
- * over all simple-update truncations of the sweep that drop a value above the cutoff
- * (DBL_MAX if none does).  A small gap means the kept subspace of that cut is sensitive to
- * perturbations such as FP32 rounding.  td_network_record_gaps(net, 1) enables it (the
- * next call allocates a device buffer of B doubles; enable it before a stream capture);
- * td_network_last_gaps copies the first n values of the last call to gap_dev (device double
- * [n]), asynchronously on `stream`; TD_ERR_INVALID if recording is off or n exceeds the
- * last call's B. */
-td_status td_network_record_gaps(td_network* net, int32_t enable);
-td_status td_network_last_gaps(td_network* net, double* gap_dev, int64_t n, void* stream);
-
 td_status td_network_get_info(const td_network* net, td_network_info* info);
 
 /* Diagnostic: run the sweep of Sec. 4 on the first min(B, wave) shots up to the end of the

@@ -159,17 +159,6 @@ class Network:
                                         C.byref(sm), C.byref(cr), C.byref(ms), self._stream(stream)))
         return {"final_threads": th.value, "final_smem": bool(sm.value), "chunk_rows": cr.value, "ms": ms.value}
 
-    def record_gaps(self, enable: bool = True):
-        """Keep each shot's smallest relative truncation gap in later decode calls."""
-        check(self._lib.td_network_record_gaps(self._h, int(bool(enable))))
-
-    def last_gaps(self, n, device="cuda", stream=None):
-        """Smallest relative truncation gap of each of the first n shots of the last call."""
-        import torch
-        out = torch.empty(n, dtype=torch.float64, device=device)
-        check(self._lib.td_network_last_gaps(self._h, C.c_void_p(out.data_ptr()), n, self._stream(stream)))
-        return out
-
     def debug_sweep(self, det, n_gates, stream=None):
         """Bond weights [B, n_bonds, chi] and log-scale slots after the first n_gates gates
         (rounded up to a whole gate round); returns (lam, logacc, applied)."""

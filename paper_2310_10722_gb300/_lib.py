@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NONLOCAL", 3: "TD_ER
 
 EXPORTS = ["td_default_options", "td_build_network", "td_coset_logprob", "td_decode",
            "td_coset_logprob_host", "td_grad_logprob", "td_grad_logprob_forced", "td_network_set_schedule",
-           "td_network_tune", "td_network_record_gaps", "td_network_last_gaps", "td_network_get_info", "td_debug_sweep",
+           "td_network_tune", "td_network_get_info", "td_debug_sweep",
            "td_network_profile", "td_network_get_work", "td_coset_logprob_static", "td_free_network",
            "td_last_error"]
 
@@ -80,10 +80,6 @@ def load(path: str | None = None):
     lib.td_network_set_schedule.restype = C.c_int
     lib.td_network_tune.argtypes = [vp, vp, C.c_int64, vp, vp, vp, vp, vp]
     lib.td_network_tune.restype = C.c_int
-    lib.td_network_record_gaps.argtypes = [vp, C.c_int32]
-    lib.td_network_record_gaps.restype = C.c_int
-    lib.td_network_last_gaps.argtypes = [vp, vp, C.c_int64, vp]
-    lib.td_network_last_gaps.restype = C.c_int
     lib.td_network_get_info.argtypes = [vp, C.POINTER(td_network_info)]
     lib.td_network_get_info.restype = C.c_int
     lib.td_debug_sweep.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, vp, C.POINTER(C.c_int32), vp]

@@ -53,12 +53,6 @@ struct td_network {
   int64_t fscr_elems = 0;       // final-contraction scratch per shot (largest candidate layout)
   int smem_optin = 0;
   int32_t chunk_rows = td::kChunkRows;   // rows per Gram / update job
-  // per-shot smallest relative truncation gap of the last call (td_network_record_gaps)
-  bool record_gaps = false;
-  bool gaps_active = false;     // set around the run() of td_coset_logprob / td_decode
-  double* d_gap = nullptr;
-  size_t d_gap_cap = 0;
-  int64_t last_B = 0;
   size_t bytes = 0;
   int64_t launches_per_wave = 0;
   std::vector<void*> allocs;
@@ -351,7 +345,6 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     a.vs = vs;
     a.ovr = ovr;
     a.chunk_rows = net->chunk_rows;
-    a.gap = (net->gaps_active && !final_scratch && !vs) ? net->d_gap + w0 : nullptr;
     const bool f64 = P.precision == TD_FP64;
     cudaError_t e;
     {
@@ -433,21 +426,10 @@ static td_status check_call(td_network* net, const void* det, int64_t B) {
   return TD_OK;
 }
 
-// Per-shot gap recording: the buffer grows to the call's B (outside any stream capture the
-// caller may run: enable recording before capturing).
-static td_status prepare_gaps(td_network* net, int64_t B) {
-  if (!net->record_gaps) return TD_OK;
-  net->last_B = B;
-  if ((size_t)B <= net->d_gap_cap) return TD_OK;
-  if (!net->reserve(net->d_gap, net->d_gap_cap, (size_t)B)) return fail(TD_ERR_OOM, "gap buffer");
-  return TD_OK;
-}
-
 td_status td_coset_logprob(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev, void* stream) {
   g_err.clear();
   td_status s = check_call(net, det_dev, B);
   if (s != TD_OK) return s;
-  if ((s = prepare_gaps(net, B)) != TD_OK) return s;
   if (B > 0 && !logp_dev) return fail(TD_ERR_INVALID, "null output buffer");
   return run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -458,11 +440,7 @@ td_status td_decode(td_network* net, const uint8_t* det_dev, int64_t B, int32_t*
   td_status s = check_call(net, det_dev, B);
   if (s != TD_OK) return s;
   if (B > 0 && !decision_dev) return fail(TD_ERR_INVALID, "null decision buffer");
-  if ((s = prepare_gaps(net, B)) != TD_OK) return s;
-  net->gaps_active = net->record_gaps;
-  s = run(net, det_dev, B, nullptr, decision_dev, margin_dev, reinterpret_cast<cudaStream_t>(stream));
-  net->gaps_active = false;
-  return s;
+  return run(net, det_dev, B, nullptr, decision_dev, margin_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
 td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_t B, double* logp_host, void* stream) {
@@ -967,23 +945,6 @@ td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, in
   if (chunk_rows) *chunk_rows = best_c;
   if (ms_best) *ms_best = best;
   return TD_OK;
-}
-
-td_status td_network_record_gaps(td_network* net, int32_t enable) {
-  g_err.clear();
-  if (!net) return fail(TD_ERR_INVALID, "null network");
-  net->record_gaps = enable != 0;
-  return TD_OK;
-}
-
-td_status td_network_last_gaps(td_network* net, double* gap_dev, int64_t n, void* stream) {
-  g_err.clear();
-  if (!net || (n > 0 && !gap_dev)) return fail(TD_ERR_INVALID, "null argument");
-  if (!net->record_gaps || !net->d_gap || n > net->last_B) return fail(TD_ERR_INVALID, "no gaps recorded for that many shots");
-  if (n == 0) return TD_OK;
-  cudaError_t e = cudaMemcpyAsync(gap_dev, net->d_gap, sizeof(double) * n, cudaMemcpyDeviceToDevice,
-                                  reinterpret_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? TD_OK : cuda_fail(e, "gap copy");
 }
 
 td_status td_debug_sweep(td_network* net, const uint8_t* det_dev, int64_t B, int32_t n_gates, double* lam_dev,

@@ -256,14 +256,8 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
     double srt[2 * kMaxChi];
     for (int j = 0; j < rB; ++j) srt[j] = sm.sv[sm.order[j]];
     int k = 0;
-    const int nmin = rB < rA ? rB : rA;
-    if (srt[0] > 0.0) k = team_keep_count<double>(srt, nmin, Dn, a.svd_cutoff, a.multiplet_rtol);
+    if (srt[0] > 0.0) k = team_keep_count<double>(srt, rB < rA ? rB : rA, Dn, a.svd_cutoff, a.multiplet_rtol);
     meta[0] = k;
-    if (a.gap && k > 0 && k < nmin && srt[k] > a.svd_cutoff * srt[0]) {
-      // relative gap at the cut (non-negative doubles order like their bit patterns)
-      const double gp = (srt[k - 1] - srt[k]) / srt[k - 1];
-      atomicMin(reinterpret_cast<unsigned long long*>(a.gap + b), (unsigned long long)__double_as_longlong(gp));
-    }
   }
   tm.sync();
   const int k = meta[0];

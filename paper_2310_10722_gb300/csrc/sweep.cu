@@ -31,7 +31,6 @@ __global__ void k_init(SweepArgs a, const LocalDesc* __restrict__ locals0, int S
   for (int w = threadIdx.x; w < a.nbonds * a.chi; w += blockDim.x) lam[w] = (w % a.chi == 0) ? 1.0 : 0.0;
   double* la = a.logacc + (int64_t)b * a.nslots;
   for (int w = threadIdx.x; w < a.nslots; w += blockDim.x) la[w] = 0.0;
-  if (a.gap && threadIdx.x == 0) a.gap[b] = DBL_MAX;
 }
 
 template <typename R>

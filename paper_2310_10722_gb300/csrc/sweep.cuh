@@ -25,9 +25,6 @@ struct SweepArgs {
   const Override* ovr;
   int32_t layer;            // current layer (local operators)
   int32_t gate_base;        // global index of the round's first gate (core)
-  // per shot: the smallest relative gap (s_{k-1} - s_k) / s_{k-1} at a truncation that drops
-  // a value above the cutoff (null: not kept); reset by k_init
-  double* gap;
   // recording for the reverse sweep (null otherwise)
   double* rec_sc;           // [B][S] scale of this layer's site-local operators
   double* rec_core;         // [gates][B][kCoreRec(chi)] truncation cores (indexed by global gate)
