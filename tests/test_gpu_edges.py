@@ -1,0 +1,83 @@
+"""Edge cases of the CUDA path against the oracle: impossible syndromes (probability 0),
+the smallest and largest bond caps, empty batches of the gradient, all-zero syndromes."""
+import numpy as np
+import pytest
+
+from td_inputs import point_sector_3d, rotated_phenomenological, sample_shots
+from oracle import exact, su
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def td():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_10722_gb300 as td
+    from paper_2310_10722_gb300 import build, _lib
+    import os
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    return td
+
+
+def _close(a, b):
+    both = np.isneginf(a) & np.isneginf(b)
+    return np.where(both, 0.0, np.abs(a - b)).max()
+
+
+def test_impossible_syndromes_read_minus_infinity(td):
+    """3D point sector d=3: random detector bits violate the checks' local dependencies for
+    most patterns; those have P(m) = 0 and read log p = -inf in both classes.  Possible ones
+    match the exact values; the gradient ignores the impossible shots."""
+    import torch
+    dem = point_sector_3d(3, 0.05)
+    rng = np.random.default_rng(41)
+    det = rng.integers(0, 2, size=(32, dem.n_det), dtype=np.uint8)
+    sampled, _ = sample_shots(dem, 8, seed=42)
+    det = np.concatenate([det, sampled])
+    ref = exact.transfer_matrix(dem, det)
+    net = td.Network.from_dem(dem, chi=8, chi_mps=64)
+    d = torch.from_numpy(det).cuda()
+    out = net.coset_logprob(d).cpu().numpy()
+    assert np.isneginf(ref).all(axis=1).sum() > 0            # the case is exercised
+    assert _close(out, ref) < 1e-9
+    logP, g = net.grad_logprob(d)
+    assert np.isfinite(g.cpu().numpy()).all()
+    possible = ~np.isneginf(ref).all(axis=1)
+    gref = exact.grad_total_logprob(dem, det[possible]).sum(axis=0) / len(det)   # mean over all B
+    assert np.abs(g.cpu().numpy() - gref).max() / max(1.0, np.abs(gref).max()) < 1e-9
+
+
+@pytest.mark.parametrize("chi,chi_mps", [(1, 1), (1, 4), (2, 2)])
+def test_smallest_bond_caps(td, chi, chi_mps):
+    import torch
+    dem = rotated_phenomenological(5, 4, 0.03, 0.03)
+    det, _ = sample_shots(dem, 6, seed=43)
+    net = td.Network.from_dem(dem, chi=chi, chi_mps=chi_mps)
+    out = net.coset_logprob(torch.from_numpy(det).cuda()).cpu().numpy()
+    assert _close(out, su.su_logprob(dem, det, chi=chi, chi_mps=chi_mps)) < 1e-6
+
+
+def test_largest_bond_cap_is_exact(td):
+    """chi = 32 (the largest supported) on rotated d=3 with 3 noisy rounds: untruncated."""
+    import torch
+    dem = rotated_phenomenological(3, 3, 0.05, 0.04)
+    det, _ = sample_shots(dem, 16, seed=44)
+    net = td.Network.from_dem(dem, chi=32, chi_mps=8)
+    out = net.coset_logprob(torch.from_numpy(det).cuda()).cpu().numpy()
+    assert _close(out, exact.transfer_matrix(dem, det)) < 1e-9
+
+
+def test_all_zero_syndromes_and_empty_gradient(td):
+    import torch
+    dem = rotated_phenomenological(5, 4, 0.03, 0.03)
+    det = np.zeros((4, dem.n_det), dtype=np.uint8)
+    net = td.Network.from_dem(dem, chi=8, chi_mps=8)
+    out = net.coset_logprob(torch.from_numpy(det).cuda()).cpu().numpy()
+    assert np.all(out[:, 0] == out[0, 0]) and np.all(out[:, 1] == out[0, 1])   # identical shots, identical values
+    assert out[0, 0] > out[0, 1]                                            # no error is the likely class
+    assert _close(out, su.su_logprob(dem, det, chi=8, chi_mps=8)) < 1e-6
+    logP, g = net.grad_logprob(torch.zeros((0, dem.n_det), dtype=torch.uint8, device="cuda"))
+    assert logP.shape == (0,) and np.all(g.cpu().numpy() == 0.0)
