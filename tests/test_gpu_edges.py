@@ -28,26 +28,33 @@ def _close(a, b):
 
 
 def test_impossible_syndromes_read_minus_infinity(td):
-    """3D point sector d=3: random detector bits violate the checks' local dependencies for
-    most patterns; those have P(m) = 0 and read log p = -inf in both classes.  Possible ones
-    match the exact values; the gradient ignores the impossible shots."""
+    """3D point sector d=3 with every mechanism at detector 0 switched off (rate 0): a shot
+    with that detector set has P(m) = 0 and reads log p = -inf in both classes; the others
+    match the exact values; the gradient (mean over all B) gets nothing from the impossible
+    shots and stays finite."""
     import torch
-    dem = point_sector_3d(3, 0.05)
-    rng = np.random.default_rng(41)
-    det = rng.integers(0, 2, size=(32, dem.n_det), dtype=np.uint8)
-    sampled, _ = sample_shots(dem, 8, seed=42)
-    det = np.concatenate([det, sampled])
+    base = point_sector_3d(3, 0.05)
+    p = base.p.copy()
+    for j, dets in enumerate(base.mech_dets):
+        if 0 in dets:
+            p[j] = 0.0
+    dem = base.with_rates(p)
+    det, _ = sample_shots(dem, 16, seed=42)
+    bad = det.copy()
+    bad[:, 0] ^= 1
+    det = np.concatenate([det, bad])
     ref = exact.transfer_matrix(dem, det)
+    possible = ~np.isneginf(ref).all(axis=1)
+    assert possible.sum() == 16 and not possible[16:].any()
     net = td.Network.from_dem(dem, chi=8, chi_mps=64)
     d = torch.from_numpy(det).cuda()
     out = net.coset_logprob(d).cpu().numpy()
-    assert np.isneginf(ref).all(axis=1).sum() > 0            # the case is exercised
     assert _close(out, ref) < 1e-9
     logP, g = net.grad_logprob(d)
-    assert np.isfinite(g.cpu().numpy()).all()
-    possible = ~np.isneginf(ref).all(axis=1)
-    gref = exact.grad_total_logprob(dem, det[possible]).sum(axis=0) / len(det)   # mean over all B
-    assert np.abs(g.cpu().numpy() - gref).max() / max(1.0, np.abs(gref).max()) < 1e-9
+    g = g.cpu().numpy()
+    assert np.isfinite(g).all() and np.isneginf(logP.cpu().numpy()[16:]).all()
+    gref = exact.grad_total_logprob(dem, det[possible]).sum(axis=0) / len(det)
+    assert np.abs(g - gref).max() / max(1.0, np.abs(gref).max()) < 1e-9
 
 
 @pytest.mark.parametrize("chi,chi_mps", [(1, 1), (1, 4), (2, 2)])
