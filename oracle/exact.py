@@ -219,9 +219,12 @@ def _parity_weights(group, p, C):
 
 
 def total_logprob(logp_cls: np.ndarray) -> np.ndarray:
-    """log P(m) = log sum_L p_{m,L}."""
+    """log P(m) = log sum_L p_{m,L}  (-inf when every class has probability 0)."""
     mx = np.max(logp_cls, axis=1)
-    return mx + np.log(np.exp(logp_cls - mx[:, None]).sum(axis=1))
+    fin = np.isfinite(mx)
+    safe = np.where(fin, mx, 0.0)
+    with np.errstate(divide="ignore"):
+        return np.where(fin, safe + np.log(np.exp(logp_cls - safe[:, None]).sum(axis=1)), mx)
 
 
 def grad_total_logprob(dem, det_bits: np.ndarray) -> np.ndarray:

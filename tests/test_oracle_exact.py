@@ -167,3 +167,11 @@ def test_css_bitflip_equals_dem():
     # detector index of the DEM: detectors are the Z checks in the same order
     np.testing.assert_allclose(T[:, :, 0], table, atol=1e-15)
     assert np.all(T[:, :, 1] == 0)
+
+
+def test_total_logprob_of_impossible_syndrome_is_minus_infinity():
+    """P(m) = sum_L p_{m,L} = 0 gives log P = -inf (not NaN)."""
+    from oracle import exact
+    lp = np.array([[-np.inf, -np.inf], [np.log(0.25), np.log(0.5)], [-np.inf, np.log(0.1)]])
+    out = exact.total_logprob(lp)
+    assert np.isneginf(out[0]) and abs(out[1] - np.log(0.75)) < 1e-15 and abs(out[2] - np.log(0.1)) < 1e-15
