@@ -80,6 +80,7 @@ struct td_network {
   int32_t* d_round_first = nullptr;
   int32_t* d_layer_round = nullptr;
   int32_t grad_wave = 0;
+  int64_t gfscr_elems = 0;      // per-shot elements of d_gfscr as allocated
   double *d_hist = nullptr, *d_rec_core = nullptr, *d_rec_sc = nullptr, *d_rec_fin = nullptr, *d_adj_scr = nullptr,
          *d_gfscr = nullptr, *d_Kbar = nullptr, *d_pbar = nullptr, *d_Rbar = nullptr, *d_glogp = nullptr;
   td::AdjArgs adj{};
@@ -689,7 +690,10 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
   const size_t budget = net->opt.mem_budget ? net->opt.mem_budget : (size_t(16) << 30);
   int64_t gw = std::min<int64_t>({(int64_t)net->wave, std::max<int64_t>(B, 1),
                                    std::max<int64_t>(1, (int64_t)(budget / std::max<size_t>(per_shot, 1)))});
-  if (net->d_hist && gw <= net->grad_wave) return TD_OK;   // smaller calls reuse the buffers
+  // smaller calls reuse the buffers, unless the final contraction's layout (set by the
+  // launch schedule) needs more scratch than was allocated
+  if (net->d_hist && gw <= net->grad_wave && G.scratch_elems <= net->gfscr_elems) return TD_OK;
+  gw = std::max<int64_t>(gw, net->grad_wave);
   for (double** pp : {&net->d_hist, &net->d_rec_core, &net->d_rec_sc, &net->d_rec_fin, &net->d_adj_scr, &net->d_gfscr,
                       &net->d_Kbar, &net->d_pbar, &net->d_Rbar, &net->d_glogp})
     if (*pp) {
@@ -729,6 +733,7 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
       return cuda_fail(e, "reverse-sweep descriptor upload");
   }
   net->grad_wave = (int32_t)gw;
+  net->gfscr_elems = G.scratch_elems;
   return TD_OK;
 }
 

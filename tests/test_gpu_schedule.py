@@ -56,3 +56,19 @@ def test_tune_picks_a_candidate_and_keeps_results(td):
     assert np.abs(after - before).max() < 1e-3
     with pytest.raises(Exception):
         net.set_schedule(384, 2048)
+
+
+def test_gradient_after_a_schedule_change(td):
+    """A gradient call, then a schedule with a larger final-contraction layout, then another
+    gradient call: both equal the exact gradient (the reverse sweep's scratch follows)."""
+    import torch
+    dem = rotated_phenomenological(3, 2, 0.05, 0.04)
+    det, _ = sample_shots(dem, 8, seed=9)
+    d = torch.from_numpy(det).cuda()
+    net = td.Network.from_dem(dem, chi=16, chi_mps=32)
+    ref = exact.grad_total_logprob(dem, det).mean(axis=0)
+    for sched in ((256, 4096, True), (1024, 512, False), (512, 1024, True)):
+        net.set_schedule(sched[0], sched[1], sched[2])
+        _, g = net.grad_logprob(d)
+        g = g.cpu().numpy()
+        assert np.abs(g - ref).max() / max(1.0, np.abs(ref).max()) < 1e-9
