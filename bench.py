@@ -400,15 +400,17 @@ def main():
     # captured once in a CUDA graph and replayed (one network per code size)
     if extra is not None:
         from td_inputs import point_sector_3d
-        per, chi_u = 32, 16
+        # 152 shots per code size: one shot per SM in the final contraction (one block per
+        # shot), as in a large mixed batch; each network tuned on its first 32 shots
+        per, chi_u = 152, 16
         nets_u, dets_u, outs_u, sched_u = [], [], [], []
         for dcode in (5, 7, 9, 11):
             dem_u = point_sector_3d(dcode, 0.1)
             du, _ = sample_shots(dem_u, per, seed=4000 + dcode)
             nets_u.append(td.Network.from_dem(dem_u, chi=chi_u, chi_mps=8, precision=td.TD_FP32,
-                                              mem_budget=16 << 30))
+                                              mem_budget=48 << 30))
             dets_u.append(torch.from_numpy(du).cuda())
-            sched_u.append(nets_u[-1].tune(dets_u[-1]))     # per-(d, chi) schedule, outside the capture
+            sched_u.append(nets_u[-1].tune(dets_u[-1][:32]))     # per-(d, chi) schedule, outside the capture
             outs_u.append(torch.empty((per, 2), dtype=torch.float64, device="cuda"))
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
