@@ -168,3 +168,22 @@ def test_grad_full_size_sampled(td):
         lp_ref, g_ref = reverse.reverse_grad_total_logprob(dem, det[b:b + 1], 8, 8, jac=jac)
         assert abs(logP[0] - lp_ref[0]) < 1e-6
         assert _rel(g, g_ref[0]) < 1e-5, _rel(g, g_ref[0])
+
+
+def test_grad_largest_bond_cap_exact(td):
+    """chi = 32 (the largest supported, untruncated here): the exact gradient."""
+    dem = log_uniform_rates(rotated_phenomenological(3, 3, 0.05, 0.04), seed=33)
+    det, _ = sample_shots(dem, 8, seed=34)
+    logP, g, _ = _grad(td, dem, det, chi=32, chi_mps=8)
+    assert _rel(g, exact.grad_total_logprob(dem, det).mean(axis=0)) < 1e-9
+
+
+def test_grad_chi16_truncated_matches_oracle_differences(td):
+    """chi = 16 with truncation (rotated d=5, 3 noisy rounds): central differences of the
+    oracle's same-chi sweep in sampled rates."""
+    dem = rotated_phenomenological(5, 3, 0.06, 0.05)
+    det, _ = sample_shots(dem, 2, seed=35)
+    logP, g, _ = _grad(td, dem, det, chi=16, chi_mps=16)
+    js = np.arange(0, dem.n_mech, max(1, dem.n_mech // 10))
+    fd = _fd_same_chi(dem, det, 16, 16, js)
+    assert np.abs(g[js] - fd).max() / max(1.0, np.abs(fd).max()) < 1e-6
