@@ -326,6 +326,118 @@ __global__ void __launch_bounds__(256) k_gram_sym8(SweepArgs a, const GateDesc* 
   }
 }
 
+// Gram pass for bond dimensions 9..16 using the symmetry of G+ and G-.  Eight lanes per row;
+// lane sub holds the row with its index permuted by q -> q ^ 2 sub (assembled by shuffles),
+// and every lane accumulates the same list of 24 entries (i, j) of its copy, which is entry
+// (i ^ 2 sub, j ^ 2 sub) of the Gram.  The list holds one entry of each orbit of the 136
+// entries i <= j under the eight maps q -> q ^ 2s: (0, j) for every j and (1, j) for odd j;
+// the orbits of the entries (i, i ^ 2s) have four elements and are computed twice, with
+// identical results.  24 products per row and Gram instead of 32.
+namespace {
+__device__ constexpr int kSym16I[24] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 1};
+__device__ constexpr int kSym16J[24] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 1, 3, 5, 7, 9, 11, 13, 15};
+}  // namespace
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram_sym16(SweepArgs a, const GateDesc* __restrict__ gates,
+                                                    double* __restrict__ gram, int64_t n_jobs, int nchunk,
+                                                    int chunk_rows) {
+  constexpr int LPR = 8, BPL = 2, RPW = 4, NE = 24;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int64_t job = (int64_t)blockIdx.x * wpb + warp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int chi = a.chi;
+  double* lamv = reinterpret_cast<double*>(smem_raw) + (size_t)warp * kMaxBonds * chi;
+  if (job >= n_jobs) return;
+  const Job jb = decode_job(job, nchunk, a.B);
+  const GateDesc& gd = gates[jb.gi];
+  const SideDesc sd = gd.side[jb.side];
+  const int D = gd.D;
+  const double* lamb = a.lam + (int64_t)jb.b * a.nbonds * chi;
+  for (int w = lane; w < kMaxBonds * chi; w += 32) {
+    const int k = w / chi;
+    lamv[w] = (k < sd.nb) ? lamb[sd.bond[k] * chi + (w % chi)] : 1.0;
+  }
+  __syncwarp();
+  const Pairs pg = side_pairs(sd.P, sd.mask);
+  const int OI = sd.outer * sd.inner;
+  const int rows = pg.npairs * OI;
+  const int r_begin = jb.ch * chunk_rows;
+  const int r_end = min(rows, r_begin + chunk_rows);
+  const int64_t SZ = (int64_t)OI * D;
+  const T* gin = reinterpret_cast<const T*>(a.gamma) + (int64_t)jb.b * a.shot_elems + sd.in_off;
+  const int slot = lane / LPR, sub = lane % LPR, row0 = slot * LPR;
+  double accp[NE], accm[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    accp[e] = 0.0;
+    accm[e] = 0.0;
+  }
+  for (int r0 = r_begin; r0 < r_end; r0 += RPW) {
+    const int r = r0 + slot;
+    const bool live = r < r_end;
+    double yo[BPL], zo[BPL];
+    {
+      int pr = 0, o = 0, i = 0;
+      double w = 0.0;
+      if (live) {
+        pr = r / OI;
+        const int oi = r % OI;
+        o = oi / sd.inner;
+        i = oi % sd.inner;
+        w = row_weight<double>(sd, o, i, lamv, chi);
+      }
+      const T* plo = gin + pg.lo(pr) * SZ + (int64_t)o * D * sd.inner + i;
+      const T* phi = gin + pg.hi(pr) * SZ + (int64_t)o * D * sd.inner + i;
+#pragma unroll
+      for (int k = 0; k < BPL; ++k) {
+        const int q = sub * BPL + k;
+        double lo = 0.0, hi = 0.0;
+        if (live && q < D) {
+          lo = double(plo[(int64_t)q * sd.inner]);
+          hi = double(phi[(int64_t)q * sd.inner]);
+        }
+        yo[k] = (lo + hi) * w;
+        zo[k] = (lo - hi) * w;
+      }
+    }
+    double y[16], z[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int src = row0 + ((q >> 1) ^ sub);   // element q of the copy is element q ^ 2 sub of the row
+      y[q] = __shfl_sync(0xffffffffu, yo[q & 1], src);
+      z[q] = __shfl_sync(0xffffffffu, zo[q & 1], src);
+    }
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      accp[e] += y[kSym16I[e]] * y[kSym16J[e]];
+      accm[e] += z[kSym16I[e]] * z[kSym16J[e]];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < NE; ++e)
+#pragma unroll
+    for (int o = 16; o >= LPR; o >>= 1) {
+      accp[e] += __shfl_xor_sync(0xffffffffu, accp[e], o);
+      accm[e] += __shfl_xor_sync(0xffffffffu, accm[e], o);
+    }
+  if (slot == 0) {
+    double* out = gram + (jb.gb * nchunk + jb.ch) * 4 * chi * chi + (int64_t)(2 * jb.side) * chi * chi;
+    const int sw = 2 * sub;
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      const int i = kSym16I[e] ^ sw, j = kSym16J[e] ^ sw;
+      if (i < D && j < D) {
+        out[i * D + j] = accp[e];
+        out[j * D + i] = accp[e];
+        out[chi * chi + i * D + j] = accm[e];
+        out[chi * chi + j * D + i] = accm[e];
+      }
+    }
+  }
+}
+
 // Update pass: Gamma_new[lo] = Y T+ + Z T-, Gamma_new[hi] = Y T+ - Z T-, in FP64 arithmetic
 // for both storage types (T), the result rounded to the storage type.
 template <typename T, int DMAX>
@@ -430,6 +542,10 @@ static cudaError_t gram_launch(const SweepArgs& a, const GateDesc* g, int count,
     cudaError_t e = cudaFuncSetAttribute(k_gram_sym8<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_gram_sym8<T><<<blocks, wpb * 32, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
+  } else if constexpr (DMAX == 16) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_sym16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_sym16<T><<<blocks, wpb * 32, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_gram<T, DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
