@@ -540,6 +540,10 @@ def main():
         "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
         "roofline": roof,
         "kernel_time_share": {k: round(v[0] / tot_ms, 4) for k, v in prof.items()},
+        # share of the timed device time in kernels that compute in FP64 (the Gram, update,
+        # truncation core and site-local operators; the final contraction is FP32 here)
+        "fp64_time_share": round(sum(prof[k][0] for k in ("local", "gram", "core", "update") if k in prof) / tot_ms, 4),
+        "tensor_pipe": "unused: every contraction of the sweep needs FP64 accumulation (DESIGN.md section 8)",
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),
