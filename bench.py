@@ -543,7 +543,7 @@ def main():
         # share of the timed device time in kernels that compute in FP64 (the Gram, update,
         # truncation core and site-local operators; the final contraction is FP32 here)
         "fp64_time_share": round(sum(prof[k][0] for k in ("local", "gram", "core", "update") if k in prof) / tot_ms, 4),
-        "tensor_pipe": "unused: every contraction of the sweep needs FP64 accumulation (DESIGN.md section 8)",
+        "tensor_pipe": "unused: every contraction of the sweep needs FP64 accumulation",
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk.summary(),

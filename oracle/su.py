@@ -9,7 +9,7 @@ cut by a truncated SVD (Sec. 4; simple-update steps as in the reference the pape
 for it).  The remaining 2D network is contracted by an MPS sweep with bond chi_mps
 (Sec. 4, and chi_MPS of Sec. 5).
 
-Readings taken where the paper is silent (each also listed in the design doc):
+Readings taken where the paper is silent:
   * Boundary state: PEPS amplitude psi(sigma) over sigma_s = the bit of the vertical
     (inter-layer) mechanism entering site s of the current layer; starts at sigma = 0.
   * A layer: detector flips and single-detector mechanisms act on one site; vertical
