@@ -109,3 +109,25 @@ def test_reverse_sweep_truncated_matches_differences():
         b = su.su_logprob(dem.with_rates(pm), det, 2, 8)
         fd = (np.logaddexp(a[:, 0], a[:, 1]) - np.logaddexp(b[:, 0], b[:, 1])) / (2 * h)
         np.testing.assert_allclose(g[:, j], fd, rtol=1e-6, atol=1e-6)
+
+
+def test_reverse_sweep_planted_mistake_is_caught(monkeypatch):
+    """Dropping the truncated SVD's projection term (I - U U^T) U-bar S^-1 V^T from the
+    oracle's reverse sweep breaks its agreement with the exact gradient even without
+    truncation (the kept subspaces rotate with the rates): the pins see such a slip."""
+    dem = repetition_phenomenological(5, 3, 0.07, 0.03)
+    det, _ = sample_shots(dem, 1, seed=11)
+    good = reverse._svd_adjoint
+
+    def slipped(U, s, V, k, Ubar, Vbar, Sbar, rel=1e-13):
+        full = good(U, s, V, k, Ubar, Vbar, Sbar, rel)
+        r = int(np.count_nonzero(s > rel * s[0]))
+        Uf, Vf, sf = U[:, :r], V[:, :r], s[:r]
+        Ub = np.zeros((U.shape[0], r))
+        if Ubar is not None:
+            Ub[:, :k] = Ubar
+        return full - (Ub - Uf @ (Uf.T @ Ub)) @ np.diag(1 / sf) @ Vf.T
+
+    monkeypatch.setattr(reverse, "_svd_adjoint", slipped)
+    _, g = reverse.reverse_grad_total_logprob(dem, det, chi=256, chi_mps=1024)
+    assert np.abs(g - exact.grad_total_logprob(dem, det)).max() > 1e-3
