@@ -359,6 +359,11 @@ def main():
                 "max_dlogp_coset": float(d.max()), "median_dlogp_coset": float(d.median()),
                 "p99_dlogp_coset": float(torch.quantile(dflat, 0.99)),
                 "frac_shots_within_1e-3": float((dflat <= 1e-3).double().mean()),
+                # the coset the FP64 path ranks first (the decision's coset), and the other one:
+                # FP32 arithmetic in the shared final contraction errs by ~eps32 exp(margin)
+                # on the minority coset
+                "max_dlogp_majority_coset": float(d.gather(1, (lp64[:, 1] > lp64[:, 0]).long()[:, None]).max()),
+                "max_dlogp_minority_coset": float(d.gather(1, (lp64[:, 1] <= lp64[:, 0]).long()[:, None]).max()),
                 "max_dlogP_total": float(torch.where(torch.isinf(tot32) & torch.isinf(tot64),
                                                      torch.zeros_like(tot32), (tot32 - tot64).abs()).max()),
                 "decisions_differ": dec_diff,
