@@ -45,7 +45,6 @@ def workload(chi):
 # ---------------------------------------------------------------- CPU oracle leg
 def _oracle_chunk(args):
     first, n, chi = args
-    import numpy as np
     from oracle import su
     from td_inputs import rotated_phenomenological, sample_shots
     dem = rotated_phenomenological(D_CODE, ROUNDS, P_DATA, Q_MEAS)
@@ -262,7 +261,6 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.chi)
 
-    import numpy as np
     import torch
     import torch.distributed as dist
     import paper_2310_10722_gb300 as td

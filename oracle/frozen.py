@@ -39,7 +39,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg
 
-from .su import SUPlan, PEPS, ZeroProbability, keep_count, plan_det, _scale_axis
+from .su import SUPlan, PEPS, ZeroProbability, keep_count, plan_det
 
 
 def _local_matrix(plan, m, s, t):
