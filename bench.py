@@ -531,7 +531,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 truncation cores and log-sum)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (FP64 arithmetic in the sweep on FP32 storage; FP32 final contraction; FP64 log-sum)",
         "data": "synthetic",
         "config": {"workload": workload(chi), "shots_per_gpu": SHOTS, "chi": chi, "chi_mps": chi,
                    "precision": "fp32", "wave": info["wave"], "workspace_gb": info["workspace_bytes"] / 1e9,
