@@ -150,7 +150,10 @@ td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_
  * on a device shares the one array and leaves its contents behind (nothing in it needs to
  * start at zero): calls whose work overlaps on the GPU -- on different streams, or from
  * different threads -- race on it and must be serialised by the caller.  Every GPU that
- * loads the library holds the array until the process exits. */
+ * loads the library holds the array until the process exits.  The looked-up address is
+ * kept for the life of the process: after cudaDeviceReset on a device it is stale, so do
+ * not use this call on that device again in the same process.  Kernel timing
+ * (td_network_profile) records none of this call's launches (it would create events). */
 td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
                                   void* stream);
 

@@ -485,7 +485,13 @@ td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64
   void* scr = nullptr;
   cudaError_t e = td::static_final_scratch(&scr);
   if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");
-  return run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream), scr);
+  // kernel timing (td_network_profile) creates CUDA events on demand: this call records
+  // none, so that it stays free of every allocation
+  const bool prof = net->profiling;
+  net->profiling = false;
+  s = run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream), scr);
+  net->profiling = prof;
+  return s;
 }
 
 // ---- gradient pass ----------------------------------------------------------------------
