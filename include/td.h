@@ -46,7 +46,7 @@ typedef enum {
   TD_ERR_NONLOCAL = 2,     /* a mechanism is not single-site, grid-bond or vertical */
   TD_ERR_OOM = 3,          /* device or host allocation failed */
   TD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
-  TD_ERR_TIMEOUT = 5,      /* reserved: a bounded device wait gave up */
+  TD_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (reported by td_network_check) */
   TD_ERR_NUMERIC = 6,      /* reserved: non-finite intermediate */
   TD_ERR_UNSUPPORTED = 7   /* valid input outside what this build implements */
 } td_status;
@@ -56,8 +56,11 @@ typedef enum {
   TD_FP32 = 1,   /* FP32 storage of the site tensors; the sweep (Gram, update, site operators,
                     truncation cores) computes in FP64 from it, the final boundary-MPS
                     contraction in FP32, the log-sum in FP64 */
-  TD_TF32 = 2    /* reserved: tensor-core contractions with FP32 accumulation; rejected by
-                    td_build_network with TD_ERR_UNSUPPORTED */
+  TD_TC = 2      /* as TD_FP32, with the Gram pass on the tcgen05 tensor cores for bond
+                    dimensions 4..16: each value is split into eight exact 6-bit BF16 slices
+                    below a per-column power-of-two bound, slice products are summed exactly
+                    in FP32 (TMEM) over at most 1024 rows and combined in FP64 (inputs kept
+                    to 2^-47 of the bound); other bond dimensions use the FP64 Gram */
 } td_precision;
 
 /* DEM triple (H, p, l) of Sec. 2.4, host memory, CSR by rows. */
@@ -222,6 +225,12 @@ td_status td_network_tune(td_network* net, const uint8_t* det_dev, int64_t B, in
 
 td_status td_network_get_info(const td_network* net, td_network_info* info);
 
+/* Device status of the network's kernels (a property of this library): synchronises
+ * `stream`, then returns and clears the status that a kernel recorded since the last check
+ * -- TD_ERR_TIMEOUT when a tensor-core kernel's bounded wait for its MMAs gave up (its
+ * results of that call are not valid) -- or TD_OK.  td_coset_logprob_host checks it too. */
+td_status td_network_check(td_network* net, void* stream);
+
 /* Diagnostic: run the sweep of Sec. 4 on the first min(B, wave) shots up to the end of the
  * gate round that contains gate n_gates-1 (site-local operators of a layer run before its
  * first round), then copy the bond weights and the log-scale accumulators.
@@ -252,6 +261,14 @@ td_status td_network_profile(td_network* net, int32_t enable, double* ms, int64_
  * factorisations (symmetric eigensolver with vectors 9n^3; SVD of m x n, m >= n, with both
  * factors 4m^2 n + 8m n^2 + 9n^3).  fp64_flops = the part of flops done in FP64. */
 td_status td_network_get_work(const td_network* net, double* bytes, double* flops, double* fp64_flops);
+
+/* Measurement helper for roofline denominators (no counterpart in the paper): the fused
+ * multiply-add throughput of the current GPU's CUDA cores in FP64 (fp64 != 0) or FP32, in
+ * TFLOP/s (2 flops per FMA), from one timed launch (CUDA events on `stream`) of eight
+ * independent FMA chains of `iters` steps per thread, eight 256-thread blocks per SM, after
+ * an untimed one.  Synchronous; allocates a small output buffer.  Errors: TD_ERR_INVALID
+ * (null tflops, iters < 1), TD_ERR_CUDA. */
+td_status td_measure_fma_peak(int32_t fp64, int32_t iters, double* tflops, void* stream);
 
 /* Release the network and its device workspace (NULL is a no-op).  The caller must
  * ensure no enqueued work still uses it. */

@@ -12,9 +12,9 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import TD_FP32, TD_FP64, TD_TF32, TDError, check
+from ._lib import TD_FP32, TD_FP64, TD_TC, TDError, check
 
-__all__ = ["Network", "TDError", "TD_FP64", "TD_FP32", "TD_TF32", "load_library"]
+__all__ = ["Network", "TDError", "TD_FP64", "TD_FP32", "TD_TC", "load_library"]
 
 
 def load_library():
@@ -73,6 +73,11 @@ class Network:
         inf = _lib.td_network_info()
         check(self._lib.td_network_get_info(self._h, C.byref(inf)))
         return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def check(self, stream=None):
+        """td_network_check: synchronise the stream and raise if a kernel recorded an error
+        status (TD_ERR_TIMEOUT: a bounded device wait gave up) since the last check."""
+        check(self._lib.td_network_check(self._h, self._stream(stream)))
 
     @staticmethod
     def _stream(stream):
@@ -198,6 +203,16 @@ class Network:
             self.close()
         except Exception:
             pass
+
+
+def fma_peak_tflops(fp64: bool = True, iters: int = 1 << 16, stream=None) -> float:
+    """td_measure_fma_peak: measured FMA throughput (TFLOP/s) of the current GPU."""
+    import torch
+    lib = load_library()
+    out = C.c_double(0.0)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    check(lib.td_measure_fma_peak(1 if fp64 else 0, int(iters), C.byref(out), C.c_void_p(s.cuda_stream)))
+    return out.value
 
 
 def mean_logprob(net: "Network", det, p):

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(HERE, "libtd.so")
 
 TD_OK, TD_ERR_INVALID, TD_ERR_NONLOCAL, TD_ERR_OOM, TD_ERR_CUDA, TD_ERR_TIMEOUT, TD_ERR_NUMERIC, \
     TD_ERR_UNSUPPORTED = range(8)
-TD_FP64, TD_FP32, TD_TF32 = 0, 1, 2
+TD_FP64, TD_FP32, TD_TC = 0, 1, 2
 STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NONLOCAL", 3: "TD_ERR_OOM", 4: "TD_ERR_CUDA",
                 5: "TD_ERR_TIMEOUT", 6: "TD_ERR_NUMERIC", 7: "TD_ERR_UNSUPPORTED"}
 
@@ -17,7 +17,7 @@ EXPORTS = ["td_default_options", "td_build_network", "td_coset_logprob", "td_dec
            "td_coset_logprob_host", "td_grad_logprob", "td_grad_logprob_forced", "td_network_set_schedule",
            "td_network_tune", "td_network_get_info", "td_debug_sweep",
            "td_network_profile", "td_network_get_work", "td_coset_logprob_static", "td_free_network",
-           "td_last_error"]
+           "td_network_check", "td_measure_fma_peak", "td_last_error"]
 
 
 class td_dem(C.Structure):
@@ -90,6 +90,10 @@ def load(path: str | None = None):
     lib.td_network_get_work.restype = C.c_int
     lib.td_coset_logprob_static.argtypes = [vp, vp, C.c_int64, vp, vp]
     lib.td_coset_logprob_static.restype = C.c_int
+    lib.td_network_check.argtypes = [vp, vp]
+    lib.td_network_check.restype = C.c_int
+    lib.td_measure_fma_peak.argtypes = [C.c_int32, C.c_int32, vp, vp]
+    lib.td_measure_fma_peak.restype = C.c_int
     lib.td_free_network.argtypes = [vp]
     lib.td_free_network.restype = None
     lib.td_last_error.argtypes = []

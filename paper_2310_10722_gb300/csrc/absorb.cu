@@ -22,10 +22,13 @@
 // against the FP64 oracle at chi = 16 (rotated d = 9), FP32 Grams moved log p by up to 0.3;
 // FP64 Grams with an FP32 update still by 0.2 on one shot in eight; FP64 arithmetic on FP32
 // storage stays within 2e-4.  Forming Y = lo + hi and Z = lo - hi in FP32 alone cost 1e-3.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
 #include "sweep.cuh"
+#include "tc.cuh"
 
 namespace td {
 
@@ -585,6 +588,334 @@ cudaError_t launch_update2(const SweepArgs& a, const GateDesc* g, int count, int
     case 16: return update_launch<T, 16>(a, g, count, tbuf, nchunk, chunk_rows, st);
     default: return update_launch<T, 32>(a, g, count, tbuf, nchunk, chunk_rows, st);
   }
+}
+
+
+// ---- Gram pass on the tensor cores (tcgen05), exact BF16 slices ------------------------------
+// For FP32 storage.  G+ = Y^T Y and G- = Z^T Z of one job (gate side, shot, row chunk) as
+// products of BF16 slices on the tensor cores, exact up to the 2^-47 truncation of the
+// inputs (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by
+// using fast routines of matrix multiplication", 2012: split the operands into slices whose
+// pairwise products are summed without rounding, then add the slice products in higher
+// precision).
+//   1. Column bound: b_q = max over the chunk's rows of (|lo| + |hi|) w (FP32), and the
+//      scale 2^E_q > 2 b_q, so every |y| and |z| of column q is below 2^E_q.
+//   2. Per block of KB rows, y = (lo + hi) w and z = (lo - hi) w are formed as exact FP32
+//      pairs (TwoSum of lo, hi; TwoProduct with w = w1 + w2, the row weight split into two
+//      FP32 parts; the dropped term is below 2^-47 |y|), scaled by 2^-E_q and cut into
+//      kTcSlices integer slices of 6 bits each (y 2^-E = sum_i t_i 64^-(i+1); the slices of
+//      the two FP32 parts are added, |t_i| <= 126, exact in BF16).
+//   3. The slices of a block are stored as the K-major operand S (row a = (slice i, column
+//      q), K = the block's rows) and one MMA chain accumulates S S^T in TMEM (FP32): its
+//      entries sum products of integers below 126^2 = 15876 over at most kTcGroupRows = 1024
+//      rows, so every partial sum is an integer below 2^24 and exact.
+//   4. Every 1024 rows the accumulator is read (tcgen05.ld) and combined in FP64:
+//      G[q][q'] = 2^(E_q + E_q') sum_(i,j) 64^-(i+j+2) (S S^T)[(i,q),(j,q')].
+// DPAD = 16 (bond dimensions 9..16): two operands (Y, Z) of 128 rows, two 128-column
+// accumulators.  DPAD = 8 (bond dimensions <= 8): one operand with Y's 64 rows above Z's.
+namespace {
+constexpr int kTcSlices = 8;
+constexpr int kTcGroupRows = 1024;
+constexpr int kTcThreads = 256;
+constexpr int kTcMaxPolls = 1 << 22;   // bounded MMA-completion wait, then TD_ERR_TIMEOUT
+template <int DPAD>
+struct TcCfg;
+template <>
+struct TcCfg<8> { static constexpr int KB = 256, NACC = 1, NCOL = 128; };
+template <>
+struct TcCfg<16> { static constexpr int KB = 128, NACC = 2, NCOL = 256; };
+
+template <int DPAD>
+constexpr size_t tc_operand_bytes() { return (size_t)TcCfg<DPAD>::NACC * 128 * TcCfg<DPAD>::KB * 2; }
+// dynamic shared memory: operands, the block's row weights [KB][2] (FP32 pairs), the
+// environment lambdas [kMaxBonds][chi] (FP64); padded so that at most two blocks share an SM
+// (two 256-column TMEM accumulators fill the SM's 512 columns)
+template <int DPAD>
+size_t tc_smem_bytes(int chi) {
+  const size_t need = tc_operand_bytes<DPAD>() + (size_t)TcCfg<DPAD>::KB * 8 + (size_t)kMaxBonds * chi * 8;
+  return std::max<size_t>(need, 100 * 1024);
+}
+
+// Slices of v = x1 + x2 (x1, x2 already scaled into (-1, 1)): t_i = trunc of the next six
+// bits of each part, summed.
+__device__ __forceinline__ void tc_slices(float x1, float x2, float (&t)[kTcSlices]) {
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i) {
+    x1 *= 64.f;
+    x2 *= 64.f;
+    const float a1 = truncf(x1), a2 = truncf(x2);
+    x1 -= a1;
+    x2 -= a2;
+    t[i] = a1 + a2;
+  }
+}
+
+// 2^e as a double for -1022 <= e <= 1023 (exact, integer operations only).
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// (lo + s hi) w as an FP32 pair, s = +1 or -1: exact sum, then the product with w1 + w2.
+__device__ __forceinline__ void tc_pair(float lo, float hi, float w1, float w2, float& y1, float& y2) {
+  const float s1 = lo + hi;
+  const float bb = s1 - lo;
+  const float s2 = (lo - (s1 - bb)) + (hi - bb);
+  const float p = s1 * w1;
+  const float e = fmaf(s1, w1, -p);
+  y1 = p;
+  y2 = e + fmaf(s1, w2, s2 * w1);
+}
+}  // namespace
+
+template <int DPAD>
+__global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateDesc* __restrict__ gates,
+                                                        double* __restrict__ gram, int64_t n_jobs, int nchunk,
+                                                        int chunk_rows) {
+  using Cfg = TcCfg<DPAD>;
+  constexpr int KB = Cfg::KB, NACC = Cfg::NACC, NCOL = Cfg::NCOL;
+  constexpr uint32_t IDESC = tc::idesc_bf16(128, 128);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_holder;
+  __shared__ unsigned int colbits[DPAD];
+  __shared__ int colexp[DPAD];
+  __shared__ float colscale[DPAD];
+  unsigned char* opnd = smem_raw;
+  float* wt = reinterpret_cast<float*>(smem_raw + tc_operand_bytes<DPAD>());
+  double* lamv = reinterpret_cast<double*>(wt + 2 * KB);
+  double* red = reinterpret_cast<double*>(smem_raw);   // end-of-job reduction (aliases the operands)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int chi = a.chi;
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  if (warp == 0) tc::tmem_alloc(&tmem_holder, NCOL);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_holder;
+  uint32_t phase = 0;
+  bool failed = false;
+  const int qi = tid % DPAD, kg = tid / DPAD;   // slicing item: column qi, rows 8 kg .. 8 kg + 7
+  for (int64_t job = blockIdx.x; job < n_jobs && !failed; job += gridDim.x) {
+    const Job jb = decode_job(job, nchunk, a.B);
+    const GateDesc& gd = gates[jb.gi];
+    const SideDesc sd = gd.side[jb.side];
+    const int D = gd.D;
+    const double* lamb = a.lam + (int64_t)jb.b * a.nbonds * chi;
+    for (int w = tid; w < kMaxBonds * chi; w += kTcThreads) {
+      const int k = w / chi;
+      lamv[w] = (k < sd.nb) ? lamb[sd.bond[k] * chi + (w % chi)] : 1.0;
+    }
+    if (tid < DPAD) colbits[tid] = 0u;
+    __syncthreads();
+    const Pairs pg = side_pairs(sd.P, sd.mask);
+    const int OI = sd.outer * sd.inner;
+    const int rows = pg.npairs * OI;
+    const int r_begin = jb.ch * chunk_rows;
+    const int r_end = min(rows, r_begin + chunk_rows);
+    const int64_t SZ = (int64_t)OI * D;
+    const int inner = sd.inner;
+    const float* gin = reinterpret_cast<const float*>(a.gamma) + (int64_t)jb.b * a.shot_elems + sd.in_off;
+    // 1. column bounds
+    {
+      float cm[DPAD];
+#pragma unroll
+      for (int c = 0; c < DPAD; ++c) cm[c] = 0.f;
+      for (int r = r_begin + tid; r < r_end; r += kTcThreads) {
+        const int pr = r / OI, oi = r % OI, o = oi / inner, i = oi % inner;
+        const float w = (float)row_weight<double>(sd, o, i, lamv, chi);
+        const float* plo = gin + pg.lo(pr) * SZ + (int64_t)o * D * inner + i;
+        const float* phi = gin + pg.hi(pr) * SZ + (int64_t)o * D * inner + i;
+#pragma unroll
+        for (int c = 0; c < DPAD; ++c)
+          if (c < D) cm[c] = fmaxf(cm[c], (fabsf(plo[(int64_t)c * inner]) + fabsf(phi[(int64_t)c * inner])) * w);
+      }
+#pragma unroll
+      for (int c = 0; c < DPAD; ++c) {
+        float v = cm[c];
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0 && v > 0.f) atomicMax(&colbits[c], __float_as_uint(v));
+      }
+    }
+    __syncthreads();
+    if (tid < DPAD) {
+      const float bnd = __uint_as_float(colbits[tid]);
+      int e = -100;
+      if (bnd > 0.f) {
+        frexpf(bnd, &e);   // bnd < 2^e
+        e = min(max(e + 1, -100), 100);
+      }
+      colexp[tid] = e;
+      colscale[tid] = ldexpf(1.f, -e);
+    }
+    double part[DPAD];
+#pragma unroll
+    for (int c = 0; c < DPAD; ++c) part[c] = 0.0;
+    int grp_rows = 0;
+    const int nblk = (r_end - r_begin + KB - 1) / KB;
+    for (int blk = 0; blk < nblk; ++blk) {
+      const int rb = r_begin + blk * KB;
+      // 2. row weights of the block as FP32 pairs
+      for (int k = tid; k < KB; k += kTcThreads) {
+        const int r = rb + k;
+        double w = 0.0;
+        if (r < r_end) {
+          const int oi = r % OI;
+          w = row_weight<double>(sd, oi / inner, oi % inner, lamv, chi);
+        }
+        const float w1 = (float)w;
+        wt[2 * k] = w1;
+        wt[2 * k + 1] = (float)(w - (double)w1);
+      }
+      __syncthreads();
+      {
+        float lo8[8], hi8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int r = rb + kg * 8 + u;
+          lo8[u] = 0.f;
+          hi8[u] = 0.f;
+          if (qi < D && r < r_end) {
+            const int pr = r / OI, oi = r % OI, o = oi / inner, i = oi % inner;
+            const int64_t off = (int64_t)o * D * inner + (int64_t)qi * inner + i;
+            lo8[u] = gin[pg.lo(pr) * SZ + off];
+            hi8[u] = gin[pg.hi(pr) * SZ + off];
+          }
+        }
+        const float sc = colscale[qi];
+#pragma unroll
+        for (int pt = 0; pt < 2; ++pt) {
+          uint32_t pk[kTcSlices][4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float t0[kTcSlices], t1[kTcSlices];
+            float y1, y2;
+            const int k0 = kg * 8 + 2 * v;
+            tc_pair(lo8[2 * v], pt ? -hi8[2 * v] : hi8[2 * v], wt[2 * k0], wt[2 * k0 + 1], y1, y2);
+            tc_slices(y1 * sc, y2 * sc, t0);
+            tc_pair(lo8[2 * v + 1], pt ? -hi8[2 * v + 1] : hi8[2 * v + 1], wt[2 * k0 + 2], wt[2 * k0 + 3], y1, y2);
+            tc_slices(y1 * sc, y2 * sc, t1);
+#pragma unroll
+            for (int i = 0; i < kTcSlices; ++i) {
+              const __nv_bfloat162 h = __floats2bfloat162_rn(t0[i], t1[i]);
+              pk[i][v] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+          }
+          unsigned char* base = opnd + (NACC == 2 ? (size_t)pt * 128 * KB * 2 : 0);
+          const int row_off = (NACC == 2) ? 0 : pt * 64;
+#pragma unroll
+          for (int i = 0; i < kTcSlices; ++i) {
+            const int arow = row_off + i * DPAD + qi;
+            *reinterpret_cast<uint4*>(base + tc::kmajor_off(arow, kg * 8, KB)) =
+                make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+          }
+        }
+      }
+      // 3. one MMA chain over the block
+      tc::fence_smem_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        const uint32_t b0 = tc::smem_u32(opnd);
+#pragma unroll 1
+        for (int ks = 0; ks < KB / 16; ++ks)
+#pragma unroll
+          for (int p = 0; p < NACC; ++p) {
+            const uint64_t d = tc::sdesc(b0 + (uint32_t)(p * 128 * KB * 2 + ks * 256), 128, (KB / 8) * 128);
+            tc::mma_bf16(tmem + (uint32_t)(p * 128), d, d, IDESC, (grp_rows > 0 || ks > 0) ? 1u : 0u);
+          }
+        tc::commit(&mbar);
+      }
+      const bool ok = tc::mbar_wait(&mbar, phase, kTcMaxPolls);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+      grp_rows += KB;
+      if (grp_rows >= kTcGroupRows || blk == nblk - 1) {
+        // 4. read the accumulator(s) and add the slice products in FP64
+        if (NACC == 2) {
+          const int sub = warp & 3, sel = warp >> 2;
+          const int ia = (sub * 32 + lane) / DPAD;
+#pragma unroll 1
+          for (int j = 0; j < kTcSlices; ++j) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(sel * 128 + j * 16), v);
+            const double scl = pow2d(-6 * (ia + j + 2));
+#pragma unroll
+            for (int c = 0; c < DPAD; ++c) part[c] += (double)v[c] * scl;
+          }
+        } else if (warp < 4) {
+          const int arow = warp * 32 + lane;
+          const int pa = arow / 64, ia = (arow % 64) / DPAD;
+#pragma unroll 1
+          for (int jj = 0; jj < kTcSlices / 2; ++jj) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(pa * 64 + jj * 16), v);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const double scl = pow2d(-6 * (ia + 2 * jj + h + 2));
+#pragma unroll
+              for (int c = 0; c < DPAD; ++c) part[c] += (double)v[h * DPAD + c] * scl;
+            }
+          }
+        }
+        grp_rows = 0;
+        tc::fence_before_sync();
+      }
+      __syncthreads();
+    }
+    if (failed) break;
+    // end of job: sum the partials of the slice lanes (i) of every (part, q)
+    if (NACC == 2) {
+      const int row = (warp >> 2) * 128 + (warp & 3) * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < DPAD; ++c) red[row * DPAD + c] = part[c];
+    } else if (warp < 4) {
+      const int row = warp * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < DPAD; ++c) red[row * DPAD + c] = part[c];
+    }
+    __syncthreads();
+    double* out = gram + (jb.gb * nchunk + jb.ch) * 4 * chi * chi + (int64_t)(2 * jb.side) * chi * chi;
+    for (int w = tid; w < 2 * D * D; w += kTcThreads) {
+      const int pt = w / (D * D), qa = (w / D) % D, qb = w % D;
+      const int rbase = (NACC == 2) ? pt * 128 : pt * 64;
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < kTcSlices; ++i) s += red[(rbase + i * DPAD + qa) * DPAD + qb];
+      out[(int64_t)pt * chi * chi + qa * D + qb] = ldexp(s, colexp[qa] + colexp[qb]);
+    }
+    __syncthreads();
+  }
+  if (failed && tid == 0 && a.status) atomicExch(a.status, (int)TD_ERR_TIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, NCOL);
+}
+
+template <int DPAD>
+static cudaError_t gram_tc_launch(const SweepArgs& a, const GateDesc* g, int count, double* gram, int nchunk,
+                                  int chunk_rows, cudaStream_t st) {
+  const int64_t n_jobs = (int64_t)count * a.B * 2 * nchunk;
+  if (n_jobs == 0) return cudaSuccess;
+  const size_t smem = tc_smem_bytes<DPAD>(a.chi);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int64_t grid = std::min<int64_t>(n_jobs, 2LL * nsm);
+  k_gram_tc<DPAD><<<(unsigned)grid, kTcThreads, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
+  return cudaGetLastError();
+}
+
+bool gram_tc_supported(int maxD) { return maxD >= 4 && maxD <= 16; }
+
+cudaError_t launch_gram_tc(const SweepArgs& a, const GateDesc* g, int count, int maxD, double* gram, int nchunk,
+                           int chunk_rows, cudaStream_t st) {
+  return maxD <= 8 ? gram_tc_launch<8>(a, g, count, gram, nchunk, chunk_rows, st)
+                   : gram_tc_launch<16>(a, g, count, gram, nchunk, chunk_rows, st);
 }
 
 template cudaError_t launch_gram2<float>(const SweepArgs&, const GateDesc*, int, int, double*, int, int, cudaStream_t);

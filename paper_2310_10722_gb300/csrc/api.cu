@@ -34,7 +34,8 @@ td_status cuda_fail(cudaError_t e, const char* what) {
 struct td_network {
   td::Plan plan;
   int32_t wave = 0;
-  size_t elem = 8;            // bytes per storage element
+  size_t elem = 8;            // bytes per storage element of the site tensors
+  static constexpr size_t felem = 8;   // bytes per element of the final contraction (FP64 on both paths)
   void* d_gamma = nullptr;
   double* d_lam = nullptr;
   double* d_logacc = nullptr;
@@ -42,6 +43,7 @@ struct td_network {
   double* d_tbuf = nullptr;
   void* d_fscr = nullptr;
   double* d_Z = nullptr;
+  int* d_status = nullptr;      // device status word (td_network_check)
   td::GateDesc* d_gates = nullptr;
   td::LocalDesc* d_locals = nullptr;
   td::FinalSite* d_finals = nullptr;
@@ -174,10 +176,22 @@ static void final_layout(td_network* net, int threads, bool allow_smem = true) {
       mV = std::max<int64_t>(mV, (int64_t)m * td::bank_ld32(m, g));
     }
   }
-  const int64_t mW = std::max<int64_t>((int64_t)cm * Dm * 2 * Dm * cmx, mV);
+  // QR-reduced cuts (n >= m): the copy of M^T (n x m, ld n), the m x m factor R and V with the
+  // leading dimensions of an m x m Jacobi, and the FP32-preconditioning scratch
+  int64_t mR = 0;
+  {
+    const int m_max = cm * Dm;
+    for (int m = 1; m <= m_max; ++m) {
+      const int g = td::team_svd_group(threads, m, m);
+      mR = std::max<int64_t>(mR, (int64_t)m * td::bank_ld32(m, g));
+    }
+  }
+  const int64_t mQ = (int64_t)cmx * Dm * 2 * cm * Dm;
+  const int64_t mP = (int64_t)(cm * Dm + 1) * cm * Dm, mT = (int64_t)cm * Dm * cm * Dm;
+  const int64_t mW = std::max<int64_t>({(int64_t)cm * Dm * 2 * Dm * cmx, mV, mR});
   const int64_t mC = (int64_t)cm * cmx * Dm * 2;
   const int64_t mS = 2LL * cm * Dm;
-  const int64_t mOrd = ((int64_t)cm * Dm * 4 + net->elem - 1) / net->elem;
+  const int64_t mOrd = ((int64_t)cm * Dm * 4 + net->felem - 1) / net->felem;
   int64_t wacc = 0;
   auto wtake = [&](int64_t n) { int64_t r = wacc; wacc += (n + 3) / 4 * 4; return r; };
   net->fin.w_F = wtake(mF);
@@ -187,9 +201,15 @@ static void final_layout(td_network* net, int threads, bool allow_smem = true) {
   net->fin.w_C1 = wtake(mC);
   net->fin.w_s = wtake(mS);
   net->fin.w_ord = wtake(mOrd);
+  // the QR copy is dead once R is extracted, before the preconditioning scratch is used
+  net->fin.w_Q = wtake(std::max<int64_t>(mQ, (mP + 3) / 4 * 4 + mT));
+  net->fin.w_P = net->fin.w_Q;
+  net->fin.w_T = net->fin.w_Q + (mP + 3) / 4 * 4;
+  net->fin.w_R = wtake(mR);
   net->fin.work_elems = wacc;
+  net->fin.precond = (P.precision == TD_FP64) ? 0 : 1;
   const size_t static_smem = 8 * 1024;   // k_final's own shared arrays
-  net->fin.use_smem = (allow_smem && (size_t)wacc * net->elem + static_smem <= (size_t)net->smem_optin) ? 1 : 0;
+  net->fin.use_smem = (allow_smem && (size_t)wacc * net->felem + static_smem <= (size_t)net->smem_optin) ? 1 : 0;
   int64_t acc = 0;
   auto take = [&](int64_t n) { int64_t r = acc; acc += (n + 3) / 4 * 4; return r; };
   net->fin.off_mps0 = take(mps_stride * P.nx);
@@ -240,7 +260,6 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   net->opt = o;
   const int chi = P.chi, cm = P.chi_mps, Dm = P.max_final_D;
   if ((int64_t)cm * Dm > 256) { delete net; return fail(TD_ERR_UNSUPPORTED, "chi_mps * final bond dimension must be <= 256"); }
-  if (o.precision == TD_TF32) { delete net; return fail(TD_ERR_UNSUPPORTED, "TF32 tensor-core path not built yet"); }
   net->elem = (o.precision == TD_FP64) ? 8 : 4;
   net->nslots = P.S + P.n_bonds + 1;
 
@@ -272,7 +291,7 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
     for (const td::Round& rd : L.rounds) max_chunks = std::max(max_chunks, td::absorb_chunks(rd.max_rows, td::kMinChunkRows));
   const size_t per_shot = P.shot_elems * net->elem + (size_t)P.n_bonds * chi * 8 + (size_t)net->nslots * 8 +
                           (size_t)P.max_round_gates * 4 * chi * chi * (8 * max_chunks + 8) +
-                          (size_t)net->fscr_elems * net->elem + 16 + (size_t)P.n_det + 16;
+                          (size_t)net->fscr_elems * net->felem + 16 + (size_t)P.n_det + 16;
   const size_t budget = o.mem_budget ? o.mem_budget : (size_t(16) << 30);
   int64_t wave = (int64_t)(budget / std::max<size_t>(per_shot, 1));
   if (o.max_wave > 0) wave = std::min<int64_t>(wave, o.max_wave);
@@ -285,14 +304,15 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
             net->alloc(net->d_logacc, (size_t)wave * net->nslots * 8) &&
             net->alloc(net->d_gram, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * 8 * max_chunks) &&
             net->alloc(net->d_tbuf, (size_t)std::max(P.max_round_gates, 1) * wave * 4 * chi * chi * 8) &&
-            net->alloc(net->d_fscr, (size_t)wave * net->fscr_elems * net->elem) &&
+            net->alloc(net->d_fscr, (size_t)wave * net->fscr_elems * net->felem) &&
             net->alloc(net->d_Z, (size_t)wave * 2 * 8) &&
             net->alloc(net->d_gates, sizeof(td::GateDesc) * P.gates.size()) &&
             net->alloc(net->d_locals, sizeof(td::LocalDesc) * P.locals.size()) &&
             net->alloc(net->d_finals, sizeof(td::FinalSite) * P.finals.size()) &&
             net->alloc(net->d_grid, sizeof(int32_t) * P.grid_site.size()) &&
             net->alloc(net->d_det_stage, (size_t)wave * P.n_det) &&
-            net->alloc(net->d_logp_stage, (size_t)wave * 2 * 8);
+            net->alloc(net->d_logp_stage, (size_t)wave * 2 * 8) &&
+            net->alloc(net->d_status, sizeof(int));
   if (!ok) { delete net; return fail(TD_ERR_OOM, "device allocation failed"); }
   cudaError_t e;
   if ((!P.gates.empty() && (e = cudaMemcpy(net->d_gates, P.gates.data(), sizeof(td::GateDesc) * P.gates.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
@@ -302,6 +322,7 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
     delete net;
     return cuda_fail(e, "descriptor upload");
   }
+  if ((e = cudaMemset(net->d_status, 0, sizeof(int))) != cudaSuccess) { delete net; return cuda_fail(e, "status init"); }
   // pageable uploads may still be in flight when cudaMemcpy returns
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) { delete net; return cuda_fail(e, "descriptor upload"); }
   int64_t launches = 1 + 2;   // init, final, finalize
@@ -346,6 +367,8 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     a.vs = vs;
     a.ovr = ovr;
     a.chunk_rows = net->chunk_rows;
+    a.tc = P.precision == TD_TC ? 1 : 0;
+    a.status = net->d_status;
     const bool f64 = P.precision == TD_FP64;
     cudaError_t e;
     {
@@ -393,7 +416,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     f.wave_first = (int32_t)w0;
     {
       td_network::Mark mk(net, TD_K_FINAL, st);
-      e = f64 ? td::launch_final<double, double>(f, st) : td::launch_final<float, float>(f, st);
+      e = f64 ? td::launch_final<double, double>(f, st) : td::launch_final<float, double>(f, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "final launch");
     td::FinalizeArgs z{};
@@ -462,9 +485,22 @@ td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_
                         cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "result copy");
   }
+  return td_network_check(net, stream);
+}
+
+td_status td_network_check(td_network* net, void* stream) {
+  if (!net) return fail(TD_ERR_INVALID, "null network");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
-  return TD_OK;
+  int code = 0;
+  if ((e = cudaMemcpy(&code, net->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "status read");
+  if (code == TD_OK) return TD_OK;
+  if ((e = cudaMemset(net->d_status, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "status reset");
+  return fail((td_status)code, code == TD_ERR_TIMEOUT ? "a tensor-core kernel gave up waiting for its MMAs; the "
+                                                        "results of the calls since the last check are not valid"
+                                                      : "a kernel recorded an error status");
 }
 
 td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
@@ -473,7 +509,7 @@ td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64
   td_status s = check_call(net, det_dev, B);
   if (s != TD_OK) return s;
   if (B > 0 && !logp_dev) return fail(TD_ERR_INVALID, "null output buffer");
-  const size_t per_shot = (size_t)net->fin.scratch_elems * net->elem;
+  const size_t per_shot = (size_t)net->fin.scratch_elems * net->felem;
   const int64_t cap = (int64_t)std::min<size_t>(td::kStaticFinalScratchBytes / std::max<size_t>(per_shot, 1),
                                                 (size_t)net->wave);
   if (B > cap)
@@ -686,6 +722,7 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
   td::FinalArgs& G = net->gfin;
   G = net->fin;
   G.use_smem = 0;
+  G.precond = 0;
   G.off_work = (net->fin.off_mps1 + mA * P.nx + 3) / 4 * 4;
   G.scratch_elems = G.off_work + net->fin.work_elems;
   G.rec_stride = fin_stride; G.rec_slot = fin_slot;
@@ -1087,7 +1124,7 @@ td_status td_network_get_work(const td_network* net, double* bytes, double* flop
     }
     mL = nL; mDn = nD; mR = nR;
   }
-  if (f64) fp64_flops[TD_K_FINAL] = flops[TD_K_FINAL];
+  fp64_flops[TD_K_FINAL] = flops[TD_K_FINAL];   // FP64 on both paths
   bytes[TD_K_FINALIZE] = (double)net->nslots * 8 + P.n_det + 16;
   return TD_OK;
 }

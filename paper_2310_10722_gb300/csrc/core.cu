@@ -63,92 +63,6 @@ __device__ __forceinline__ Team make_team(int team_threads) {
   return tm;
 }
 
-// Max |x| over the m x n column-major matrix x (ld), through a shared double slot.
-__device__ double team_absmax(const Team& tm, const double* x, int ld, int m, int n, double* slot) {
-  double v = 0.0;
-  for (int w = tm.tid; w < m * n; w += tm.nt) v = fmax(v, fabs(x[(w / m) * ld + (w % m)]));
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if (tm.tid == 0) *slot = 0.0;
-  tm.sync();
-  if ((tm.tid & 31) == 0) {
-    // benign max via compare-and-swap on the bit pattern (non-negative doubles order as integers)
-    unsigned long long* p = reinterpret_cast<unsigned long long*>(slot);
-    atomicMax(p, (unsigned long long)__double_as_longlong(v));
-  }
-  tm.sync();
-  const double r = *slot;
-  tm.sync();
-  return r;
-}
-
-// C (m x n) = A (m x k) B (k x n), all row-major with the given leading dimensions.
-template <typename R>
-__device__ __forceinline__ void team_gemm(const Team& tm, const R* A, int lda, const R* B, int ldb, R* C, int ldc,
-                                          int m, int n, int k) {
-  for (int w = tm.tid; w < m * n; w += tm.nt) {
-    const int i = w / n, j = w % n;
-    R s = R(0);
-    for (int l = 0; l < k; ++l) s += A[i * lda + l] * B[l * ldb + j];
-    C[i * ldc + j] = s;
-  }
-}
-
-// SVD of theta (m x n, column-major, lda) preconditioned by an FP32 solve (see the file
-// comment); V column-major (ldv).  F: scratch of >= 2n(2n+1) doubles (also holds the two
-// FP32 matrices), Tt: >= n*n doubles.
-__device__ void svd_precond(const Team& tm, double* A, int lda, int m, int n, double* V, int ldv, double* F,
-                            double* Tt, int* flag, double* slot) {
-  const double amax = team_absmax(tm, A, lda, m, n, slot);
-  if (!(amax > 0.0) || n < 2) {
-    team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, true);
-    return;
-  }
-  const int la32 = odd_ld(m), lv32 = odd_ld(n);
-  float* A32 = reinterpret_cast<float*>(F);
-  float* V32 = A32 + la32 * n;
-  const double sc = 1.0 / amax;
-  for (int w = tm.tid; w < m * n; w += tm.nt) {
-    const int c = w / m, r = w % m;
-    A32[c * la32 + r] = float(A[c * lda + r] * sc);
-  }
-  tm.sync();
-  team_svd_onesided<float>(tm, A32, la32, m, n, V32, lv32, flag, 30, true);
-  for (int w = tm.tid; w < n * n; w += tm.nt) {
-    const int c = w / n, r = w % n;
-    V[c * ldv + r] = double(V32[c * lv32 + r]);
-  }
-  tm.sync();
-  // Newton-Schulz: V <- V (3I - V^T V) / 2   (Tt, F: column-major, ld n)
-  for (int w = tm.tid; w < n * n; w += tm.nt) {
-    const int j = w / n, i = w % n;
-    const double* vi = V + i * ldv;
-    const double* vj = V + j * ldv;
-    double s = 0.0;
-    for (int l = 0; l < n; ++l) s += vi[l] * vj[l];
-    Tt[j * n + i] = (i == j ? 1.5 : 0.0) - 0.5 * s;
-  }
-  tm.sync();
-  for (int w = tm.tid; w < n * n; w += tm.nt) {
-    const int j = w / n, i = w % n;
-    double s = 0.0;
-    for (int l = 0; l < n; ++l) s += V[l * ldv + i] * Tt[j * n + l];
-    F[j * n + i] = s;
-  }
-  tm.sync();
-  for (int w = tm.tid; w < n * n; w += tm.nt) V[(w / n) * ldv + (w % n)] = F[w];
-  tm.sync();
-  // A <- A V   (F: column-major, ld m)
-  for (int w = tm.tid; w < m * n; w += tm.nt) {
-    const int j = w / m, i = w % m;
-    double s = 0.0;
-    for (int l = 0; l < n; ++l) s += A[l * lda + i] * V[j * ldv + l];
-    F[j * m + i] = s;
-  }
-  tm.sync();
-  for (int w = tm.tid; w < m * n; w += tm.nt) A[(w / m) * lda + (w % m)] = F[w];
-  team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, false);
-}
-
 // The four Gram blocks of item (gate, shot) in FP64: the sum, in chunk order, of the
 // partial Grams of its row chunks.
 __device__ __forceinline__ void load_gram(const Team& tm, const double* gram, int64_t item, int nchunk, int chi,

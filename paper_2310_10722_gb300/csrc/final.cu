@@ -8,6 +8,18 @@
 // truncated to chi_mps by its leading singular vectors.  The class parity p flows along
 // each row into a two-valued output leg of the last MPS tensor.  The last row is contracted
 // exactly.
+//
+// Arithmetic.  The contraction computes in FP64 on both paths (T is the storage type of the
+// site tensors it reads): the class-parity leg carries both cosets through one MPS, so FP32
+// sums and FP32 singular vectors err by ~eps32 times the majority coset's weight, a relative
+// error of ~eps32 exp(margin) on the minority coset.  Each cut's left singular vectors come
+// from a one-sided Jacobi SVD; when M^T (n x m) has at least as many rows as columns it is
+// first reduced by a Householder QR, M^T = Q R, and the Jacobi orthogonalises the m columns
+// of the m x m factor R (half-length columns; R V has orthogonal columns exactly when M^T V
+// has).  The carry is then (M^T V_k)^T from the unreduced M^T.  On the mixed path the
+// Jacobi of R is preconditioned by an FP32 solve and finished by FP64 sweeps run to
+// convergence (svd_precond).  The gradient pass's recorded forward keeps the unreduced
+// Jacobi on M^T (its records are M^T V and V).
 #include <cmath>
 #include <mutex>
 
@@ -18,7 +30,7 @@ namespace td {
 
 // F[c][l][r][d][u] of site (x, y) into F (dims into fd: L, R, D, U).  sqrt(lambda) of the
 // site's bonds is staged in slam[4][chi] first.
-template <typename R>
+template <typename T, typename R>
 __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y, R* F, int* fd, R* slam) {
   const int s = fa.grid_site[y * fa.nx + x];
   if (s < 0) {
@@ -50,7 +62,7 @@ __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y
     for (int dir = 0; dir < 4; ++dir) stride[dir] = fs.dir_pos[dir] >= 0 ? st[fs.dir_pos[dir]] : 0;
   }
   const int rest = dL * dR * dD * dU;
-  const R* g = reinterpret_cast<const R*>(fa.gamma) + (int64_t)b * fa.shot_elems + fs.off;
+  const T* g = reinterpret_cast<const T*>(fa.gamma) + (int64_t)b * fa.shot_elems + fs.off;
   tm.sync();
   for (int w = tm.tid; w < rest; w += tm.nt) {
     int e = w;
@@ -62,7 +74,7 @@ __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y
     const R wgt = slam[il] * slam[fa.chi + ir] * slam[2 * fa.chi + id] * slam[3 * fa.chi + iu];
     R a0 = R(0), a1 = R(0);
     for (int ph = 0; ph < fs.P; ++ph) {
-      const R gv = g[(int64_t)ph * rest + off];
+      const R gv = R(g[(int64_t)ph * rest + off]);
       a0 += R(Rv[ph * 2 + 0]) * gv;
       a1 += R(Rv[ph * 2 + 1]) * gv;
     }
@@ -76,7 +88,7 @@ __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y
 // One block per shot.  The work region (site tensor F, T1 / V, M^T, carries) lives in
 // shared memory when it fits, otherwise in the shot's global scratch; the boundary MPS is
 // always in global scratch.
-template <typename R>
+template <typename T, typename R>
 __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
   const int b = blockIdx.x;
   const Team tm{(int)threadIdx.x, (int)blockDim.x, 1};
@@ -95,6 +107,8 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
   __shared__ int meta[8];
   __shared__ R slam[4 * kMaxChi];
   __shared__ double logsum_s;
+  __shared__ R red_s[2];
+  __shared__ double slot_s;
   const int nx = fa.nx, ny = fa.ny;
   if (tm.tid == 0) logsum_s = 0.0;
   for (int x = tm.tid; x < nx; x += tm.nt) {
@@ -111,7 +125,7 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
     int cJ = 1, cA = 1, cL = 1;
     tm.sync();
     for (int x = 0; x < nx; ++x) {
-      build_F<R>(tm, fa, b, x, y, F, fd, slam);
+      build_F<T, R>(tm, fa, b, x, y, F, fd, slam);
       const int L = fd[0], Rr = fd[1], U = fd[3];
       const R* A = mps[cur] + (int64_t)x * fa.mps_stride;
       const int aL = mdim[cur][x][0], aD = mdim[cur][x][1], aR = mdim[cur][x][2];
@@ -171,10 +185,37 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
       R* An = mps[cur ^ 1] + (int64_t)x * fa.mps_stride;
       R* Cn = Cb[cc ^ 1];
       if (x < nx - 1 && y < ny - 1) {
-        // left singular vectors of M = MT^T: one-sided Jacobi on the m columns of MT
+        // left singular vectors of M = MT^T: one-sided Jacobi on the m columns of MT, or on
+        // the columns of the triangular factor of MT's QR (see the file comment)
         R* V = W;
-        team_svd_onesided<R>(tm, MT, ldm, n, m, V, ldv, meta + 7, 40, true);
-        team_col_norms<R>(tm, MT, ldm, n, m, sv);
+        const bool qr = !rs && m >= 2 && n >= m;
+        int ldvv = ldv;
+        if (qr) {
+          R* Qw = work + fa.w_Q;
+          R* Rk = work + fa.w_R;
+          const int ldr = bank_ld32(m, team_svd_group(tm.nt, m, m));
+          ldvv = bank_ld32(m, team_svd_group(tm.nt, m, m));
+          for (int w = tm.tid; w < m * n; w += tm.nt) Qw[(w / n) * n + w % n] = MT[(w / n) * ldm + w % n];
+          tm.sync();
+          team_qr_r<R>(tm, Qw, n, n, m, red_s);
+          for (int w = tm.tid; w < m * m; w += tm.nt) {
+            const int c = w / m, r = w % m;
+            Rk[c * ldr + r] = (r <= c) ? Qw[c * n + r] : R(0);
+          }
+          tm.sync();
+          if constexpr (sizeof(R) == 8) {
+            if (fa.precond)
+              svd_precond(tm, Rk, ldr, m, m, V, ldvv, work + fa.w_P, work + fa.w_T, meta + 7, &slot_s);
+            else
+              team_svd_onesided<R>(tm, Rk, ldr, m, m, V, ldvv, meta + 7, 40, true);
+          } else {
+            team_svd_onesided<R>(tm, Rk, ldr, m, m, V, ldvv, meta + 7, 40, true);
+          }
+          team_col_norms<R>(tm, Rk, ldr, m, m, sv);
+        } else {
+          team_svd_onesided<R>(tm, MT, ldm, n, m, V, ldv, meta + 7, 40, true);
+          team_col_norms<R>(tm, MT, ldm, n, m, sv);
+        }
         team_sort_desc<R>(tm, sv, m, ord);
         if (tm.tid == 0) {
           int k = 0;
@@ -215,11 +256,22 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
           const R inv0 = R(ldexp(1.0, -e2));
           for (int w = tm.tid; w < m * k; w += tm.nt) {
             const int ju = w / k, kk = w % k;
-            An[w] = V[ord[kk] * ldv + ju];
+            An[w] = V[ord[kk] * ldvv + ju];
           }
-          for (int w = tm.tid; w < k * n; w += tm.nt) {
-            const int kk = w / n, c = w % n;
-            Cn[w] = MT[ord[kk] * ldm + c] * inv0;
+          if (qr) {
+            // carry = (M^T V_k)^T from the unreduced M^T
+            for (int w = tm.tid; w < k * n; w += tm.nt) {
+              const int kk = w / n, c = w % n;
+              const R* vk = V + ord[kk] * ldvv;
+              R acc = R(0);
+              for (int j = 0; j < m; ++j) acc += MT[j * ldm + c] * vk[j];
+              Cn[w] = acc * inv0;
+            }
+          } else {
+            for (int w = tm.tid; w < k * n; w += tm.nt) {
+              const int kk = w / n, c = w % n;
+              Cn[w] = MT[ord[kk] * ldm + c] * inv0;
+            }
           }
           if (tm.tid == 0) {
             logsum_s += double(e2) * 0.69314718055994530942;
@@ -333,10 +385,10 @@ cudaError_t launch_final(const FinalArgs& f, cudaStream_t st) {
   size_t smem = 0;
   if (f.use_smem) {
     smem = (size_t)f.work_elems * sizeof(R);
-    cudaError_t e = cudaFuncSetAttribute(k_final<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_final<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_final<R><<<f.B, f.threads, smem, st>>>(f);
+  k_final<T, R><<<f.B, f.threads, smem, st>>>(f);
   return cudaGetLastError();
 }
 
@@ -374,6 +426,6 @@ cudaError_t static_final_scratch(void** ptr) {
 }
 
 template cudaError_t launch_final<double, double>(const FinalArgs&, cudaStream_t);
-template cudaError_t launch_final<float, float>(const FinalArgs&, cudaStream_t);
+template cudaError_t launch_final<float, double>(const FinalArgs&, cudaStream_t);
 
 }  // namespace td

@@ -72,7 +72,7 @@ td_status build_plan(const td_dem& dem, const td_layout& layout, const td_option
   }
   if (opt.chi < 1 || opt.chi > kMaxChi) { err = "chi must be in [1, 32]"; return opt.chi < 1 ? TD_ERR_INVALID : TD_ERR_UNSUPPORTED; }
   if (opt.chi_mps < 1) { err = "chi_mps must be >= 1"; return TD_ERR_INVALID; }
-  if (opt.precision < TD_FP64 || opt.precision > TD_TF32) { err = "unknown precision"; return TD_ERR_INVALID; }
+  if (opt.precision < TD_FP64 || opt.precision > TD_TC) { err = "unknown precision"; return TD_ERR_INVALID; }
   if (!(opt.svd_cutoff >= 0 && opt.svd_cutoff < 1) || !(opt.multiplet_rtol >= 0 && opt.multiplet_rtol < 1) ||
       !(opt.gram_cutoff < 1)) { err = "cutoffs must be in [0, 1)"; return TD_ERR_INVALID; }
   const int32_t n_det = dem.n_det, n_mech = dem.n_mech;

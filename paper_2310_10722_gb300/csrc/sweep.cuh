@@ -28,6 +28,8 @@ struct SweepArgs {
   // recording for the reverse sweep (null otherwise)
   double* rec_sc;           // [B][S] scale of this layer's site-local operators
   double* rec_core;         // [gates][B][kCoreRec(chi)] truncation cores (indexed by global gate)
+  int32_t tc;               // Gram pass on the tensor cores (FP32 storage, TD_TC)
+  int* status;              // device status word: a kernel that gives up writes its td_status
 };
 
 // Per-gate record of the truncation core for the reverse sweep (doubles), Dm = chi:
@@ -61,6 +63,8 @@ struct FinalArgs {
   int64_t off_work;          // work region in the global scratch (when not in shared memory)
   int64_t work_elems;        // work region size (elements)
   int64_t w_F, w_W, w_MT, w_C0, w_C1, w_s, w_ord;   // offsets inside the work region
+  int64_t w_Q, w_R, w_P, w_T;   // QR copy of M^T, its triangular factor, FP32-preconditioning scratch
+  int32_t precond;           // cut SVDs: FP32-preconditioned FP64 Jacobi (mixed path)
   int32_t use_smem;          // work region in dynamic shared memory
   int32_t threads;           // threads per block (one block per shot)
   int32_t nbonds, chi, nslots, slot;
@@ -175,6 +179,10 @@ int absorb_chunks(int max_rows, int chunk_rows);
 template <typename T>
 cudaError_t launch_gram2(const SweepArgs& a, const GateDesc* g, int count, int Dm, double* gram, int nchunk,
                          int chunk_rows, cudaStream_t st);
+// Tensor-core Gram (absorb.cu; FP32 storage, bond dimensions 4..16).
+bool gram_tc_supported(int maxD);
+cudaError_t launch_gram_tc(const SweepArgs& a, const GateDesc* g, int count, int maxD, double* gram, int nchunk,
+                           int chunk_rows, cudaStream_t st);
 template <typename T>
 cudaError_t launch_update2(const SweepArgs& a, const GateDesc* g, int count, int Dm, const double* tbuf, int nchunk,
                            int chunk_rows, cudaStream_t st);

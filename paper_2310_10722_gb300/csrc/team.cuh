@@ -403,4 +403,151 @@ __device__ __forceinline__ int team_keep_count(const R* s, int n, int chi, doubl
   return k;
 }
 
+// Max |x| over the m x n column-major matrix x (ld), through a shared double slot.
+__device__ inline double team_absmax(const Team& tm, const double* x, int ld, int m, int n, double* slot) {
+  double v = 0.0;
+  for (int w = tm.tid; w < m * n; w += tm.nt) v = fmax(v, fabs(x[(w / m) * ld + (w % m)]));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (tm.tid == 0) *slot = 0.0;
+  tm.sync();
+  if ((tm.tid & 31) == 0) {
+    // benign max via compare-and-swap on the bit pattern (non-negative doubles order as integers)
+    unsigned long long* p = reinterpret_cast<unsigned long long*>(slot);
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+  }
+  tm.sync();
+  const double r = *slot;
+  tm.sync();
+  return r;
+}
+
+// C (m x n) = A (m x k) B (k x n), all row-major with the given leading dimensions.
+template <typename R>
+__device__ __forceinline__ void team_gemm(const Team& tm, const R* A, int lda, const R* B, int ldb, R* C, int ldc,
+                                          int m, int n, int k) {
+  for (int w = tm.tid; w < m * n; w += tm.nt) {
+    const int i = w / n, j = w % n;
+    R s = R(0);
+    for (int l = 0; l < k; ++l) s += A[i * lda + l] * B[l * ldb + j];
+    C[i * ldc + j] = s;
+  }
+}
+
+// One-sided Jacobi SVD of A (m x n, column-major, lda; as team_svd_onesided) preconditioned
+// by an FP32 solve (mixed-precision Jacobi): the FP32 Jacobi runs on a copy scaled to a
+// largest entry of 1; its right factor, re-orthogonalised in FP64 by one Newton-Schulz step
+// V <- V (3I - V^T V) / 2, is applied to A in FP64, and FP64 Jacobi sweeps then run to
+// convergence from it.  The FP32 solve cannot resolve singular values below ~1e-7 of the
+// largest, so the FP64 sweeps are never cut short.  V column-major (ldv).  F: scratch of
+// >= max(m, n) * (max(m, n) + 1) doubles (it also holds the two FP32 matrices); Tt: >= n*n
+// doubles; flag: one team-shared int; slot: one team-shared double.
+__device__ inline void svd_precond(const Team& tm, double* A, int lda, int m, int n, double* V, int ldv, double* F,
+                            double* Tt, int* flag, double* slot) {
+  const double amax = team_absmax(tm, A, lda, m, n, slot);
+  if (!(amax > 0.0) || n < 2) {
+    team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, true);
+    return;
+  }
+  const int la32 = odd_ld(m), lv32 = odd_ld(n);
+  float* A32 = reinterpret_cast<float*>(F);
+  float* V32 = A32 + la32 * n;
+  const double sc = 1.0 / amax;
+  for (int w = tm.tid; w < m * n; w += tm.nt) {
+    const int c = w / m, r = w % m;
+    A32[c * la32 + r] = float(A[c * lda + r] * sc);
+  }
+  tm.sync();
+  team_svd_onesided<float>(tm, A32, la32, m, n, V32, lv32, flag, 30, true);
+  for (int w = tm.tid; w < n * n; w += tm.nt) {
+    const int c = w / n, r = w % n;
+    V[c * ldv + r] = double(V32[c * lv32 + r]);
+  }
+  tm.sync();
+  // Newton-Schulz: V <- V (3I - V^T V) / 2   (Tt, F: column-major, ld n)
+  for (int w = tm.tid; w < n * n; w += tm.nt) {
+    const int j = w / n, i = w % n;
+    const double* vi = V + i * ldv;
+    const double* vj = V + j * ldv;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += vi[l] * vj[l];
+    Tt[j * n + i] = (i == j ? 1.5 : 0.0) - 0.5 * s;
+  }
+  tm.sync();
+  for (int w = tm.tid; w < n * n; w += tm.nt) {
+    const int j = w / n, i = w % n;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += V[l * ldv + i] * Tt[j * n + l];
+    F[j * n + i] = s;
+  }
+  tm.sync();
+  for (int w = tm.tid; w < n * n; w += tm.nt) V[(w / n) * ldv + (w % n)] = F[w];
+  tm.sync();
+  // A <- A V   (F: column-major, ld m)
+  for (int w = tm.tid; w < m * n; w += tm.nt) {
+    const int j = w / m, i = w % m;
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += A[l * lda + i] * V[j * ldv + l];
+    F[j * m + i] = s;
+  }
+  tm.sync();
+  for (int w = tm.tid; w < m * n; w += tm.nt) A[(w / m) * lda + (w % m)] = F[w];
+  team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, false);
+}
+
+
+// Householder QR (Golub & Van Loan, Alg. 5.2.1): A (m x n, column-major, lda, m >= n) is
+// overwritten; on return its upper triangle A[0:n, 0:n] holds R of A = Q R (the reflector
+// vectors below the diagonal are not kept; the diagonal of R may be negative).  Each
+// column norm is summed by one warp (a fixed order, so the factor is reproducible), and
+// the reflector is applied to the remaining columns by groups of g lanes per column.
+// `red`: 2 values of team-shared scratch.
+template <typename R>
+__device__ void team_qr_r(const Team& tm, R* A, int lda, int m, int n, R* red) {
+  int g = tm.nt / (n > 1 ? n - 1 : 1);
+  g = g < 1 ? 1 : (g > 32 ? 32 : team_pow2_floor(g));
+  while (g > 1 && g > m) g >>= 1;
+  const int ngroups = tm.nt / g;
+  const int grp = tm.tid / g, gl = tm.tid % g;
+  for (int j = 0; j < n; ++j) {
+    R* a = A + (size_t)j * lda;
+    if (tm.tid < 32) {
+      R s = R(0);
+      for (int r = j + 1 + tm.tid; r < m; r += 32) s += a[r] * a[r];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (tm.tid == 0) {
+        const R x0 = a[j];
+        const R nrm = sqrt(x0 * x0 + s);
+        if (!(s > R(0))) {
+          red[0] = R(0);            // nothing below the diagonal: no reflection
+        } else {
+          const R alpha = x0 >= R(0) ? -nrm : nrm;
+          const R v0 = x0 - alpha;  // |v0| = nrm + |x0|: no cancellation
+          red[0] = R(2) / (s + v0 * v0);
+          red[1] = alpha;
+          a[j] = v0;                // v = (v0, a[j+1:m])
+        }
+      }
+    }
+    tm.sync();
+    const R tau = red[0];
+    if (tau != R(0)) {
+      for (int c0 = j + 1; c0 < n; c0 += ngroups) {
+        const int c = c0 + grp;
+        R* ac = A + (size_t)c * lda;
+        R w = R(0);
+        if (c < n)
+          for (int r = j + gl; r < m; r += g) w += a[r] * ac[r];
+        for (int o = g >> 1; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (c < n) {
+          const R f = tau * w;
+          for (int r = j + gl; r < m; r += g) ac[r] -= f * a[r];
+        }
+      }
+      tm.sync();
+      if (tm.tid == 0) a[j] = red[1];
+    }
+    tm.sync();
+  }
+}
+
 }  // namespace td
