@@ -7,12 +7,16 @@ q=0.03), 9 noisy syndrome rounds + 1 perfect round (a 40-site x 10-layer detecto
 chi_mps = chi.  One step = decode the whole batch (td_decode: site operators, gate rounds
 with truncation, final contraction, log-sum, argmax) with inputs resident on the device.
 
-Reported: syndromes/s of the mixed path (FP32 storage and contractions, FP64 truncation
-cores and log-sum) and, at the same chi, of the plain FP64 GPU path; max |d log p| between
-the two; the dominant kernel against its roofline; the CPU oracle on the host cores; the
-end-to-end rate through the host-buffer entry point.
+Reported: syndromes/s of the mixed-precision path (--precision tc: FP64 storage, the Gram
+contractions on the tcgen05 tensor cores from exact BF16 slices, FP32-preconditioned SVDs
+finished in FP64) and, at the same chi, of the plain FP64 GPU path with |d log p| of every
+coset between the two; the dominant kernel against its roofline (measured FMA peak); the CPU
+oracle on the host cores; the end-to-end rate through the host-buffer entry point; beside
+them chi = 16, the exact 3D point sector d = 3, the uneven point-sector batch in one CUDA
+graph and the reverse-sweep gradient.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--chi 8] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--chi 8] [--precision tc|fp32|fp64]
+                  [--impl reference]
 Under torchrun each rank decodes its own 4096 shots (independent replicas, no collective
 on the data path); rank 0 prints one JSON line.
 """
@@ -235,6 +239,48 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
+PRECISIONS = {"fp64": 0, "fp32": 1, "tc": 2}
+DTYPES = {"fp64": "f64",
+          "fp32": "f32 storage + bf16 tensor-core Gram slices (exact, FP32 accumulate) + f32/f64 SVDs",
+          "tc": "f64 storage + bf16 tensor-core Gram slices (exact, FP32 accumulate) + f32-preconditioned f64 SVDs"}
+
+
+def _f(x, digits=4):
+    x = float(x)
+    return x if not math.isfinite(x) or x == 0 else float(f"{x:.{digits}g}")
+
+
+def coset_stats(lp, lp64):
+    """|d log p| of every coset of lp against lp64: the FP64 path's decision coset and the
+    other one, the total log P, decisions where the FP64 margin exceeds 1e-3.  Cosets that
+    are -inf on both sides count as equal; -inf on one side only is counted apart."""
+    import torch
+    fin = torch.isfinite(lp) & torch.isfinite(lp64)
+    both_inf = torch.isinf(lp) & torch.isinf(lp64)
+    d = torch.where(fin, (lp - lp64).abs(), torch.zeros_like(lp))
+    maj = (lp64[:, 1] > lp64[:, 0]).long()
+    dmaj = d.gather(1, maj[:, None])[:, 0]
+    dmin = d.gather(1, (1 - maj)[:, None])[:, 0]
+    tot, tot64 = torch.logsumexp(lp, 1), torch.logsumexp(lp64, 1)
+    dt = torch.where(torch.isfinite(tot) & torch.isfinite(tot64), (tot - tot64).abs(), torch.zeros_like(tot))
+    dec = (lp[:, 1] > lp[:, 0]) != (lp64[:, 1] > lp64[:, 0])
+    sure = (lp64[:, 1] - lp64[:, 0]).abs() > 1e-3
+    return {"max_dlogp_coset": _f(d.max()), "max_dlogp_decision_coset": _f(dmaj.max()),
+            "max_dlogp_other_coset": _f(dmin.max()), "frac_within_1e-3": _f((d.max(1).values <= 1e-3).double().mean()),
+            "max_dlogP_total": _f(dt.max()), "inf_on_one_side": int((~fin & ~both_inf).sum()),
+            "decisions_differ_margin_gt_1e-3": int((dec & sure).sum())}
+
+
+def timed_decode(net, det, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    lp = net.coset_logprob(det)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return lp, a.elapsed_time(b)
+
+
 def main():
     global SHOTS
     ap = argparse.ArgumentParser()
@@ -242,12 +288,15 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--chi", type=int, default=8)
+    ap.add_argument("--precision", default="tc", choices=sorted(PRECISIONS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU path")
     ap.add_argument("--shots", type=int, default=SHOTS, help="shots per GPU (profiling runs use fewer)")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (reported beside the line)")
+    ap.add_argument("--chi16-shots", type=int, default=256, help="shots of the chi = 16 line")
+    ap.add_argument("--uneven-per-size", type=int, default=152, help="shots per code size of the uneven batch")
     args = ap.parse_args()
     SHOTS = args.shots
     rank = int(os.environ.get("RANK", "0"))
@@ -274,16 +323,19 @@ def main():
         if world > 1:
             dist.barrier()
 
-    chi = args.chi
+    chi, prec = args.chi, PRECISIONS[args.precision]
+    stream = torch.cuda.current_stream()
+    # measured FMA throughput of this GPU (the roofline denominators of the CUDA-core kernels)
+    fma64 = td.fma_peak_tflops(fp64=True)
+    fma32 = td.fma_peak_tflops(fp64=False)
+
     dem = rotated_phenomenological(D_CODE, ROUNDS, P_DATA, Q_MEAS)
     det_np, _ = sample_shots(dem, SHOTS, seed=SEED, first_shot=replica_first_shot(rank, SHOTS))
     det = torch.from_numpy(det_np).cuda()
-    net = td.Network.from_dem(dem, chi=chi, chi_mps=chi, precision=td.TD_FP32, mem_budget=96 << 30,
-                              max_wave=SHOTS)
+    net = td.Network.from_dem(dem, chi=chi, chi_mps=chi, precision=prec, mem_budget=96 << 30, max_wave=SHOTS)
     info = net.info()
     work = net.work()
     waves = math.ceil(SHOTS / info["wave"])
-    stream = torch.cuda.current_stream()
     # launch schedule picked by the autotuner on the first 1024 shots (outside the timed region)
     schedule = net.tune(det[:1024]) if not args.no_tune else None
 
@@ -306,9 +358,9 @@ def main():
         barrier()
         wall = time.perf_counter() - t0
     prof = net.profile(False)
+    net.check()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    dev_s = sum(step_ms) / 1000.0
-    t_max = max_over_ranks(dev_s, world, device="cuda")
+    t_max = max_over_ranks(sum(step_ms) / 1000.0, world, device="cuda")
     value = world * SHOTS * args.steps / t_max
 
     # end to end through the host-buffer entry point (pinned copies inside the timed region)
@@ -323,97 +375,88 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - te
-    e2e = {"value": world * SHOTS * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": _f(world * SHOTS * args.steps / e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(det_np.nbytes), "d2h_bytes_per_step": int(out_h.numel() * 8),
            "entry": "td_coset_logprob_host"}
 
-    # plain FP64 GPU path at the same chi, and accuracy of the mixed path against it
+    # the plain FP64 GPU path at the same chi, and every coset of the headline path against it
     fp64 = None
+    lp_head = net.coset_logprob(det)
     if not args.no_fp64:
         net64 = td.Network.from_dem(dem, chi=chi, chi_mps=chi, precision=td.TD_FP64, mem_budget=96 << 30,
-                                  max_wave=SHOTS)
-        sched64 = net64.tune(det[:1024]) if not args.no_tune else None
+                                    max_wave=SHOTS)
+        if not args.no_tune:
+            net64.tune(det[:1024])
         net64.decode(det[:256])
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        lp64 = net64.coset_logprob(det)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms64 = a.elapsed_time(b)
-        lp32 = net.coset_logprob(det)
-        d = (lp32 - lp64).abs()
-        both = torch.isinf(lp32) & torch.isinf(lp64)
-        d = torch.where(both, torch.zeros_like(d), d)
-        tot32 = torch.logsumexp(lp32, dim=1)
-        tot64 = torch.logsumexp(lp64, dim=1)
-        dec_diff = int(((lp32[:, 1] > lp32[:, 0]) != (lp64[:, 1] > lp64[:, 0])).sum())
-        dflat = d.max(dim=1).values
-        # decisions compared only where the FP64 margin exceeds the mixed path's typical error
-        margin64 = (lp64[:, 1] - lp64[:, 0]).abs()
-        sure = margin64 > 1e-3
-        dec_diff_sure = int((((lp32[:, 1] > lp32[:, 0]) != (lp64[:, 1] > lp64[:, 0])) & sure).sum())
-        fp64 = {"value": SHOTS / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64,
-                "max_dlogp_coset": float(d.max()), "median_dlogp_coset": float(d.median()),
-                "p99_dlogp_coset": float(torch.quantile(dflat, 0.99)),
-                "frac_shots_within_1e-3": float((dflat <= 1e-3).double().mean()),
-                # the coset the FP64 path ranks first (the decision's coset), and the other one:
-                # FP32 arithmetic in the shared final contraction errs by ~eps32 exp(margin)
-                # on the minority coset
-                "max_dlogp_majority_coset": float(d.gather(1, (lp64[:, 1] > lp64[:, 0]).long()[:, None]).max()),
-                "max_dlogp_minority_coset": float(d.gather(1, (lp64[:, 1] <= lp64[:, 0]).long()[:, None]).max()),
-                "max_dlogP_total": float(torch.where(torch.isinf(tot32) & torch.isinf(tot64),
-                                                     torch.zeros_like(tot32), (tot32 - tot64).abs()).max()),
-                "decisions_differ": dec_diff,
-                "decisions_differ_where_margin_gt_1e-3": dec_diff_sure, "schedule": sched64}
+        lp64, ms64 = timed_decode(net64, det, stream)
+        fp64 = {"value": _f(SHOTS / (ms64 / 1000.0)), **coset_stats(lp_head, lp64)}
         net64.close()
 
+    # roofline of the dominant kernel (largest summed device time in the timed region)
+    tot_ms = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, launches = prof[dom]
+    wb, wf, wf64 = work[dom]
+    shots_done = SHOTS * args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    if dom in ("local", "update") and prec == 1:
+        ach, peak, unit, bound = wb * shots_done / (ms / 1000.0) / 1e9, float(peaks.get("hbm_gbs", 6800.0)), "GB/s", "hbm"
+        src = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    else:
+        ach, peak, unit, bound = wf * shots_done / (ms / 1000.0) / 1e12, fma64, "TFLOP/s", "alu"
+        src = "FP64 FMA throughput measured in this run by td_measure_fma_peak (of measured)"
+    roof = {"kernel": f"k_{dom}", "bound": bound, "achieved": _f(ach), "peak": _f(peak), "unit": unit,
+            "frac": _f(ach / peak, 3), "traffic": KERNEL_TRAFFIC.get((dom, args.precision, chi)),
+            "peak_source": src, "avg_launch_ms": _f(ms / max(launches, 1)), "time_share": _f(ms / tot_ms, 3),
+            "flops_per_shot": _f(wf), "fp64_flops_per_shot": _f(wf64)}
+
     # other workloads of the same path, reported beside the headline (a few seconds each)
-    extra = None
+    extra = {}
     if not args.no_extra and rank == 0:
         from td_inputs import point_sector_3d
-        extra = {}
-
-        def rate(dem_x, shots, seed, **kw):
-            dx, _ = sample_shots(dem_x, shots, seed=seed)
-            dd = torch.from_numpy(dx).cuda()
-            nx = td.Network.from_dem(dem_x, mem_budget=32 << 30, **kw)
-            nx.coset_logprob(dd[: min(64, shots)])
+        dx, _ = sample_shots(point_sector_3d(3, 0.05), 512, seed=1000)
+        n1 = td.Network.from_dem(point_sector_3d(3, 0.05), chi=8, chi_mps=64, precision=td.TD_FP64)
+        dd = torch.from_numpy(dx).cuda()
+        n1.coset_logprob(dd[:64])
+        _, m1 = timed_decode(n1, dd, stream)
+        extra["point_d3_exact_fp64_512"] = _f(512 / (m1 / 1000.0))
+        n1.close()
+        # rotated d = 9 at chi = chi_mps = 16 on the first chi16_shots shots of the stream
+        n16 = args.chi16_shots
+        d16 = det[:n16].contiguous()
+        r16 = {}
+        lps = {}
+        for name, pv in (("fp64", 0), (args.precision, prec)):
+            nx = td.Network.from_dem(dem, chi=16, chi_mps=16, precision=pv, mem_budget=96 << 30)
+            nx.coset_logprob(d16[:8])
             torch.cuda.synchronize()
-            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ea.record(stream)
-            lp = nx.coset_logprob(dd)
-            eb.record(stream)
-            torch.cuda.synchronize()
-            ms_x = ea.elapsed_time(eb)
+            lps[name], mx = timed_decode(nx, d16, stream)
+            nx.check()
+            r16[name] = _f(n16 / (mx / 1000.0))
             nx.close()
-            return shots / (ms_x / 1000.0), lp
-
-        r1, _ = rate(point_sector_3d(3, 0.05), 512, 1000, chi=8, chi_mps=64, precision=td.TD_FP64)
-        extra["point_sector_d3_p0.05_512shots_exact_fp64"] = {"value": r1, "unit": UNIT}
-        r32, lp32x = rate(dem, 256, SEED, chi=16, chi_mps=8, precision=td.TD_FP32)
-        r64, lp64x = rate(dem, 256, SEED, chi=16, chi_mps=8, precision=td.TD_FP64)
-        dx = (lp32x - lp64x).abs()
-        dx = torch.where(torch.isinf(lp32x) & torch.isinf(lp64x), torch.zeros_like(dx), dx)
-        extra["rotated_d9_chi16_chimps8_256shots"] = {
-            "mixed": {"value": r32, "unit": UNIT}, "fp64": {"value": r64, "unit": UNIT},
-            "max_dlogp_coset_mixed_vs_fp64": float(dx.max()), "median_dlogp_coset": float(dx.median())}
+        st16 = coset_stats(lps[args.precision], lps["fp64"])
+        extra["rotated_d9_chi16_mps16"] = {"shots": n16, "fp64": r16["fp64"], args.precision: r16[args.precision],
+                                           "max_dlogp_coset": st16["max_dlogp_coset"],
+                                           "max_dlogp_decision_coset": st16["max_dlogp_decision_coset"]}
 
     # uneven batch: point-sector codes d = 5, 7, 9, 11 decoded together, their decode calls
     # captured once in a CUDA graph and replayed (one network per code size)
-    if extra is not None:
+    if not args.no_extra and rank == 0:
         from td_inputs import point_sector_3d
-        # 152 shots per code size: one shot per SM in the final contraction (one block per
-        # shot), as in a large mixed batch; each network tuned on its first 32 shots
-        per, chi_u = 152, 16
-        nets_u, dets_u, outs_u, sched_u = [], [], [], []
+        per, chi_u = args.uneven_per_size, 16
+        nets_u, dets_u, outs_u = [], [], []
         for dcode in (5, 7, 9, 11):
             dem_u = point_sector_3d(dcode, 0.1)
             du, _ = sample_shots(dem_u, per, seed=4000 + dcode)
-            nets_u.append(td.Network.from_dem(dem_u, chi=chi_u, chi_mps=8, precision=td.TD_FP32,
-                                              mem_budget=48 << 30))
+            nets_u.append(td.Network.from_dem(dem_u, chi=chi_u, chi_mps=8, precision=prec, mem_budget=48 << 30))
             dets_u.append(torch.from_numpy(du).cuda())
-            sched_u.append(nets_u[-1].tune(dets_u[-1][:32]))     # per-(d, chi) schedule, outside the capture
+            if not args.no_tune:
+                nets_u[-1].tune(dets_u[-1][:32])     # per-(d, chi) schedule, outside the capture
             outs_u.append(torch.empty((per, 2), dtype=torch.float64, device="cuda"))
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
@@ -432,12 +475,9 @@ def main():
         graph.replay()
         gb.record(stream)
         torch.cuda.synchronize()
-        extra["point_sector_uneven_d5_7_9_11_chi16_graph"] = {
-            "value": 4 * per / (ga.elapsed_time(gb) / 1000.0), "unit": UNIT, "shots": 4 * per,
-            "replay_matches_eager": all(torch.equal(a, b) for a, b in zip(ref_u, outs_u)),
-            "schedules": {f"d{dc}": sc for dc, sc in zip((5, 7, 9, 11), sched_u)},
-            "note": "p=0.1, chi=16, chi_mps=8, FP32 storage; one network per code size with its launch "
-                    "schedule picked by td_network_tune, all decode calls captured in one CUDA graph"}
+        extra["point_uneven_d5-11_chi16_mps8_graph"] = {
+            "value": _f(4 * per / (ga.elapsed_time(gb) / 1000.0)), "shots": 4 * per,
+            "replay_matches_eager": all(torch.equal(a, b) for a, b in zip(ref_u, outs_u))}
         for n_u in nets_u:
             n_u.close()
 
@@ -445,8 +485,7 @@ def main():
     # rounds + 1 perfect, per-mechanism rates log-uniform in [1e-3, 1e-2], 1024 shots per
     # GPU, by the reverse sweep (td_grad_logprob); every rank takes its own slice of the shots
     # and the per-rank gradients are combined by one all-reduce (the only collective of the
-    # gradient path).  Beside it, the forced-rate gradient (td_grad_logprob_forced, 1 + 2 x
-    # 560 decodes per shot) on 16 of the shots.
+    # gradient path)
     if not args.no_extra:
         from td_inputs import log_uniform_rates
         dem_g = log_uniform_rates(rotated_phenomenological(7, 7, 0.005, 0.005), seed=5000)
@@ -458,104 +497,52 @@ def main():
         ng.coset_logprob(ddg)
         torch.cuda.synchronize()
         barrier()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(stream)
-        lpg, gg = ng.grad_logprob(ddg)
-        ev[1].record(stream)
+        evg = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        evg[0].record(stream)
+        _, gg = ng.grad_logprob(ddg)
+        evg[1].record(stream)
         ng.coset_logprob(ddg)
-        ev[2].record(stream)
+        evg[2].record(stream)
         torch.cuda.synchronize()
-        t_g = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1000.0, world, "cuda")
-        t_d = max_over_ranks(ev[1].elapsed_time(ev[2]) / 1000.0, world, "cuda")
-        g_all = mean_over_ranks(gg, g_shots, world, "cuda")
-        gres = {"value": world * g_shots / t_g, "unit": "gradient shots/s",
-                "seconds_per_1024_shots": t_g, "decode_seconds_same_shots_fp64": t_d,
-                "gradient_over_decode_time": t_g / t_d, "rates": dem_g.n_mech,
-                "grad_abs_max": float(g_all.abs().max())}
-        # forced-rate gradient on 16 shots (mixed-precision decodes) and the reverse sweep on
-        # the same shots: they differ by the truncation error of the forced networks only
-        nf = td.Network.from_dem(dem_g, chi=8, chi_mps=8, precision=td.TD_FP32, mem_budget=32 << 30)
-        nf.grad_logprob(ddg[:1], method="forced")
-        torch.cuda.synchronize()
-        ev[0].record(stream)
-        _, gf = nf.grad_logprob(ddg[:16], method="forced")
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        _, gr16 = ng.grad_logprob(ddg[:16])
-        gres["forced_rate_method"] = {"value": 16 / (ev[0].elapsed_time(ev[1]) / 1000.0), "unit": "gradient shots/s",
-                                      "decodes_per_shot": 1 + 2 * dem_g.n_mech,
-                                      "max_abs_diff_vs_reverse_rel_to_max": float((gf - gr16).abs().max()
-                                                                                  / gr16.abs().max())}
+        t_g = max_over_ranks(evg[0].elapsed_time(evg[1]) / 1000.0, world, "cuda")
+        t_d = max_over_ranks(evg[1].elapsed_time(evg[2]) / 1000.0, world, "cuda")
+        mean_over_ranks(gg, g_shots, world, "cuda")
+        gres = {"value": _f(world * g_shots / t_g), "unit": "gradient shots/s", "over_decode_time": _f(t_g / t_d, 3)}
         if rank == 0 and world == 1 and not args.no_cpu:
-            gres["cpu_baseline"] = cpu_grad_baseline()
-        gres["note"] = (f"{g_shots} shots per GPU, chi = chi_mps = 8 (chi = 32 of the workload is out of reach: "
-                        "~7 min per decode); reverse sweep in FP64: recorded forward + per-shot adjoint")
+            gres["cpu_oracle"] = _f(cpu_grad_baseline()["value"])
         ng.close()
-        nf.close()
-        if extra is not None:
-            extra["grad_rotated_d7_7rounds_loguniform_chi8"] = gres
-
-    # roofline of the dominant kernel (largest summed device time in the timed region)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    fp32_alu = 152 * 128 * 2 * 2.07e9 / 1e12          # TF/s: SMs x FP32 lanes x FMA x max clock
-    fp64_alu = 1.25                                      # TF/s, nominal GB300 FP64
-    tot_ms = sum(v[0] for v in prof.values())
-    dom = max(prof, key=lambda k: prof[k][0])
-    ms, launches = prof[dom]
-    wb, wf, wf64 = work[dom]
-    shots_done = SHOTS * args.steps
-    if dom in ("gram", "update", "local"):
-        ach = wb * shots_done / (ms / 1000.0) / 1e9
-        roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    elif wf64 >= 0.5 * wf:
-        ach = wf * shots_done / (ms / 1000.0) / 1e12
-        roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": ach, "peak": fp64_alu, "unit": "TFLOP/s",
-                "frac": ach / fp64_alu, "traffic": None,
-                "peak_source": "FP64 1.25 TFLOP/s nominal (probe measured 1.19)"}
-    else:
-        ach = wf * shots_done / (ms / 1000.0) / 1e12
-        roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": ach, "peak": fp32_alu, "unit": "TFLOP/s",
-                "frac": ach / fp32_alu, "traffic": None,
-                "peak_source": "FP32 CUDA cores 152 SMs x 128 lanes x 2 x 2.07 GHz (derived)"}
-    roof.update({"launches": launches, "avg_launch_ms": ms / max(launches, 1), "time_share": ms / tot_ms,
-                 "algorithmic_per_shot": {"bytes": wb, "flops": wf, "fp64_flops": wf64}})
+        extra["grad_rotated_d7_chi8_1024"] = gres
 
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (FP64 arithmetic in the sweep on FP32 storage; FP32 final contraction; FP64 log-sum)",
-        "data": "synthetic",
-        "config": {"workload": workload(chi), "shots_per_gpu": SHOTS, "chi": chi, "chi_mps": chi,
-                   "precision": "fp32", "wave": info["wave"], "workspace_gb": info["workspace_bytes"] / 1e9,
-                   "l2": f"not flushed: per-step working set {info['workspace_bytes'] / 1e9:.1f} GB of site tensors "
-                         "rewritten every step, far above the 129 MB L2",
-                   "parallelism": f"replicas x{world}", "schedule": schedule},
-        "wall_s_timed": wall,
-        "fp64_path": fp64,
-        "speedup_vs_fp64": (value / world / fp64["value"]) if fp64 else None,
-        "roofline": roof,
-        "kernel_time_share": {k: round(v[0] / tot_ms, 4) for k, v in prof.items()},
-        # share of the timed device time in kernels that compute in FP64 (the Gram, update,
-        # truncation core and site-local operators; the final contraction is FP32 here)
-        "fp64_time_share": round(sum(prof[k][0] for k in ("local", "gram", "core", "update") if k in prof) / tot_ms, 4),
-        "tensor_pipe": "unused: every contraction of the sweep needs FP64 accumulation",
-        "cpu_baseline": cpu,
+        "metric": METRIC, "value": _f(value), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": _f(1000.0 * t_max / args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
+        "config": {"workload": workload(chi), "precision": args.precision, "shots_per_gpu": SHOTS,
+                   "wave": info["wave"], "parallelism": f"replicas x{world}", "schedule": schedule,
+                   "l2": "not flushed: every step rewrites %.1f GB of site tensors, far above the 129 MB L2"
+                         % (info["workspace_bytes"] / 1e9)},
+        "wall_s_timed": _f(wall),
+        "kernel_time_share": {k: round(v[0] / tot_ms, 3) for k, v in prof.items() if v[0] > 0},
+        "other_workloads": extra,
+        "cpu_baseline": cpu and {k: (_f(v) if isinstance(v, float) else v) for k, v in cpu.items()},
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": int(info["launches_per_wave"] * waves * args.steps),
-        "other_workloads": extra,
+        "roofline": roof,
+        "fp64_path": fp64,
+        "speedup_vs_fp64": _f(value / world / fp64["value"], 3) if fp64 else None,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by (kernel class, precision, chi); see profiles/.  None until a
+# capture of the current kernel exists.
+KERNEL_TRAFFIC = {}
 
 
 if __name__ == "__main__":

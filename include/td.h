@@ -47,20 +47,26 @@ typedef enum {
   TD_ERR_OOM = 3,          /* device or host allocation failed */
   TD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   TD_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (reported by td_network_check) */
-  TD_ERR_NUMERIC = 6,      /* reserved: non-finite intermediate */
+  TD_ERR_NUMERIC = 6,      /* a shot met a non-finite intermediate: its logp is NaN, the batch
+                              completes (reported by td_network_check) */
   TD_ERR_UNSUPPORTED = 7   /* valid input outside what this build implements */
 } td_status;
 
 typedef enum {
-  TD_FP64 = 0,   /* FP64 storage and arithmetic everywhere (the plain FP64 GPU path) */
-  TD_FP32 = 1,   /* FP32 storage of the site tensors; the sweep (Gram, update, site operators,
-                    truncation cores) computes in FP64 from it, the final boundary-MPS
-                    contraction in FP32, the log-sum in FP64 */
-  TD_TC = 2      /* as TD_FP32, with the Gram pass on the tcgen05 tensor cores for bond
-                    dimensions 4..16: each value is split into eight exact 6-bit BF16 slices
-                    below a per-column power-of-two bound, slice products are summed exactly
-                    in FP32 (TMEM) over at most 1024 rows and combined in FP64 (inputs kept
-                    to 2^-47 of the bound); other bond dimensions use the FP64 Gram */
+  TD_FP64 = 0,   /* the plain FP64 GPU path: FP64 storage and arithmetic on the CUDA cores
+                    everywhere, every SVD an FP64 one-sided Jacobi */
+  TD_FP32 = 1,   /* mixed precision with FP32 storage of the site tensors: the Gram pass on
+                    the tcgen05 tensor cores (below), the update and site operators in FP64
+                    arithmetic, every SVD (truncation cores, zip-up cuts) FP32-preconditioned
+                    and finished by FP64 Jacobi sweeps, the final contraction and log-sum in
+                    FP64 */
+  TD_TC = 2      /* mixed precision with FP64 storage (the headline mixed path): as TD_FP32,
+                    with the site tensors kept in FP64 */
+  /* The tensor-core Gram (bond dimensions 4..16; others use the FP64 CUDA-core Gram): each
+   * value of the Gram's operands is cut into eight exact integer BF16 slices below a
+   * per-column power-of-two bound (7 bits each from FP64 storage, 56 bits; 6 bits of an
+   * exact FP32 pair from FP32 storage, 48 bits), slice products are summed exactly in FP32
+   * (TMEM) over at most 1024 rows and combined in FP64. */
 } td_precision;
 
 /* DEM triple (H, p, l) of Sec. 2.4, host memory, CSR by rows. */
@@ -86,12 +92,16 @@ typedef struct {
   int32_t chi;             /* simple-update bond cap (Sec. 4; chi_SU of Sec. 5) */
   int32_t chi_mps;         /* final boundary-MPS bond cap (chi_MPS of Sec. 5) */
   int32_t precision;       /* td_precision */
-  int32_t ckpt_stride;     /* unused: td_grad_logprob keeps every intermediate site tensor of
-                              the sweep (versioned layout) instead of checkpoints every k layers */
+  int32_t ckpt_stride;     /* td_grad_logprob: layers per checkpoint segment of the reverse sweep
+                              (<= 0 or >= the layer count: one segment, every intermediate tensor
+                              kept).  With k < T, only one segment's intermediate tensors are kept
+                              and the tensors at every segment start are checkpointed; each
+                              segment but the last is swept forward again from its checkpoint
+                              before its reverse sweep.  The gradient is identical either way. */
   double svd_cutoff;       /* keep singular values s_i > svd_cutoff * s_1 */
   double multiplet_rtol;   /* a cut inside s_k - s_{k+1} <= rtol * s_1 drops the multiplet */
   double gram_cutoff;      /* drop Gram eigen-directions below gram_cutoff * max eigenvalue;
-                              negative: 1e-15 for TD_FP64, 1e-7 otherwise */
+                              negative: 1e-15 */
   size_t mem_budget;       /* device workspace cap in bytes (0: 16 GiB) */
   int32_t max_wave;        /* shots processed per wave (0: as many as mem_budget allows) */
 } td_options;
@@ -168,8 +178,9 @@ td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64
  * changes; without truncation it is the exact gradient).
  *
  * The call runs the forward sweep once more in FP64 (whatever the network's precision)
- * with every intermediate site tensor kept and every truncation core and zip-up cut
- * recorded, then walks it backwards, one block of threads per shot: the adjoint of each
+ * with the intermediate site tensors of one segment of ckpt_stride layers kept (the inputs of
+ * every segment checkpointed, earlier segments recomputed from them) and every truncation
+ * core and zip-up cut recorded, then walks it backwards, one block of threads per shot: the adjoint of each
  * truncated SVD (the thin SVD over the nonzero singular values), of the kappa-basis
  * doubling of each gate, of the environment weights and of the site-local operators.  Its
  * result is the adjoint of every parameter object (site-local matrix, gate rate, readout),
@@ -184,8 +195,9 @@ td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64
  * for this and later calls.  logP_dev: device double [B] (log P of each shot at the rates,
  * from the FP64 sweep); grad_dev: device double [n_mech].
  * Memory: beside the decoding workspace, the recording of up to min(wave, B, mem_budget /
- * per-shot record) shots, allocated by the first call and grown by a later call with a
- * larger B; a B above mem_budget / per-shot record runs in several waves.  The
+ * per-shot record) shots -- one segment's intermediate tensors and cores, the checkpoints,
+ * the final contraction's record -- allocated by the first call and grown by a later call
+ * with a larger B; a B above mem_budget / per-shot record runs in several waves.  The
  * call synchronises `stream` (the objects' dependence on the rates is built on the host,
  * and the per-shot adjoints are summed there) and returns when the results are written.
  * Errors: TD_ERR_INVALID (null buffers, rates outside [0, 1]), TD_ERR_OOM, TD_ERR_CUDA. */
@@ -228,7 +240,9 @@ td_status td_network_get_info(const td_network* net, td_network_info* info);
 /* Device status of the network's kernels (a property of this library): synchronises
  * `stream`, then returns and clears the status that a kernel recorded since the last check
  * -- TD_ERR_TIMEOUT when a tensor-core kernel's bounded wait for its MMAs gave up (its
- * results of that call are not valid) -- or TD_OK.  td_coset_logprob_host checks it too. */
+ * results of that call are not valid), TD_ERR_NUMERIC when a shot met a non-finite
+ * intermediate (that shot's log-probabilities are NaN, the others are valid) -- or TD_OK.
+ * td_coset_logprob_host checks it too. */
 td_status td_network_check(td_network* net, void* stream);
 
 /* Diagnostic: run the sweep of Sec. 4 on the first min(B, wave) shots up to the end of the

@@ -34,7 +34,7 @@ class Network:
 
     def __init__(self, H_indptr, H_indices, L_indptr, L_indices, p, det_xyt, *, n_mech=None,
                  chi=8, chi_mps=16, precision=TD_FP64, svd_cutoff=1e-12, multiplet_rtol=1e-8,
-                 gram_cutoff=None, mem_budget=0, max_wave=0):
+                 gram_cutoff=None, mem_budget=0, max_wave=0, ckpt_stride=0):
         lib = _lib.load()
         self._lib = lib
         self._keep = [_i32(H_indptr), _i32(H_indices), _i32(L_indptr), _i32(L_indices),
@@ -56,6 +56,7 @@ class Network:
         if mem_budget:
             opt.mem_budget = mem_budget
         opt.max_wave = max_wave
+        opt.ckpt_stride = ckpt_stride
         h = C.c_void_p()
         check(lib.td_build_network(C.byref(dem), C.byref(lay), C.byref(opt), C.byref(h)))
         self._h = h

@@ -592,27 +592,28 @@ cudaError_t launch_update2(const SweepArgs& a, const GateDesc* g, int count, int
 
 
 // ---- Gram pass on the tensor cores (tcgen05), exact BF16 slices ------------------------------
-// For FP32 storage.  G+ = Y^T Y and G- = Z^T Z of one job (gate side, shot, row chunk) as
-// products of BF16 slices on the tensor cores, exact up to the 2^-47 truncation of the
-// inputs (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by
-// using fast routines of matrix multiplication", 2012: split the operands into slices whose
-// pairwise products are summed without rounding, then add the slice products in higher
-// precision).
-//   1. Column bound: b_q = max over the chunk's rows of (|lo| + |hi|) w (FP32), and the
-//      scale 2^E_q > 2 b_q, so every |y| and |z| of column q is below 2^E_q.
-//   2. Per block of KB rows, y = (lo + hi) w and z = (lo - hi) w are formed as exact FP32
-//      pairs (TwoSum of lo, hi; TwoProduct with w = w1 + w2, the row weight split into two
-//      FP32 parts; the dropped term is below 2^-47 |y|), scaled by 2^-E_q and cut into
-//      kTcSlices integer slices of 6 bits each (y 2^-E = sum_i t_i 64^-(i+1); the slices of
-//      the two FP32 parts are added, |t_i| <= 126, exact in BF16).
-//   3. The slices of a block are stored as the K-major operand S (row a = (slice i, column
-//      q), K = the block's rows) and one MMA chain accumulates S S^T in TMEM (FP32): its
-//      entries sum products of integers below 126^2 = 15876 over at most kTcGroupRows = 1024
-//      rows, so every partial sum is an integer below 2^24 and exact.
+// G+ = Y^T Y and G- = Z^T Z of one job (gate side, shot, row chunk) as products of BF16 slices
+// on the tensor cores (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication", 2012: split the operands
+// into slices whose pairwise products are summed without rounding, then add the slice
+// products in higher precision).
+//   1. Column bound: b_q = max over the chunk's rows of (|lo| + |hi|) w, and a power of two
+//      2^E_q > b_q with one bit of margin, so every |y|, |z| of column q is below 2^E_q.
+//   2. Per block of KB rows, y = (lo + hi) w and z = (lo - hi) w are cut into kTcSlices
+//      integer slices t_i below the bound: y 2^-E = sum_i t_i 2^(-BITS (i+1)) up to the last
+//      slice.  FP64 storage: y, z in FP64, the slices read off the 63-bit fixed-point value
+//      |y| 2^(63-E) (BITS = 7, |t_i| <= 127, 56 bits kept).  FP32 storage: y, z as exact FP32
+//      pairs (TwoSum of lo, hi; TwoProduct with w = w1 + w2; the dropped term is below 2^-47
+//      |y|), each part sliced by 6 bits and the slices added (BITS = 6, |t_i| <= 126, 48
+//      bits).  Every slice is an integer below 2^8, exact in BF16.
+//   3. The slices of a block form the K-major operand S (row a = (slice i, column q), K = the
+//      block's rows) and one MMA chain accumulates S S^T in TMEM (FP32).  Its entries sum
+//      products of integers below 2^14 over at most kTcGroupRows = 1024 rows: every partial
+//      sum is an integer below 2^24, exact.
 //   4. Every 1024 rows the accumulator is read (tcgen05.ld) and combined in FP64:
-//      G[q][q'] = 2^(E_q + E_q') sum_(i,j) 64^-(i+j+2) (S S^T)[(i,q),(j,q')].
+//      G[q][q'] = 2^(E_q + E_q') sum_(i,j) 2^(-BITS (i+j+2)) (S S^T)[(i,q),(j,q')].
 // DPAD = 16 (bond dimensions 9..16): two operands (Y, Z) of 128 rows, two 128-column
-// accumulators.  DPAD = 8 (bond dimensions <= 8): one operand with Y's 64 rows above Z's.
+// accumulators.  DPAD = 8 (bond dimensions 4..8): one operand with Y's 64 rows above Z's.
 namespace {
 constexpr int kTcSlices = 8;
 constexpr int kTcGroupRows = 1024;
@@ -624,10 +625,16 @@ template <>
 struct TcCfg<8> { static constexpr int KB = 256, NACC = 1, NCOL = 128; };
 template <>
 struct TcCfg<16> { static constexpr int KB = 128, NACC = 2, NCOL = 256; };
+template <typename T>
+struct TcBits;
+template <>
+struct TcBits<float> { static constexpr int BITS = 6; };
+template <>
+struct TcBits<double> { static constexpr int BITS = 7; };
 
 template <int DPAD>
 constexpr size_t tc_operand_bytes() { return (size_t)TcCfg<DPAD>::NACC * 128 * TcCfg<DPAD>::KB * 2; }
-// dynamic shared memory: operands, the block's row weights [KB][2] (FP32 pairs), the
+// dynamic shared memory: operands, the block's row weights [KB] (8 bytes each), the
 // environment lambdas [kMaxBonds][chi] (FP64); padded so that at most two blocks share an SM
 // (two 256-column TMEM accumulators fill the SM's 512 columns)
 template <int DPAD>
@@ -636,9 +643,12 @@ size_t tc_smem_bytes(int chi) {
   return std::max<size_t>(need, 100 * 1024);
 }
 
-// Slices of v = x1 + x2 (x1, x2 already scaled into (-1, 1)): t_i = trunc of the next six
-// bits of each part, summed.
-__device__ __forceinline__ void tc_slices(float x1, float x2, float (&t)[kTcSlices]) {
+// 2^e as a double for -1022 <= e <= 1023 (exact, integer operations only).
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// FP32 storage: slices of v = x1 + x2 (x1, x2 already scaled into (-1, 1)), six bits of
+// each part per slice, summed.
+__device__ __forceinline__ void tc_slices32(float x1, float x2, float (&t)[kTcSlices]) {
 #pragma unroll
   for (int i = 0; i < kTcSlices; ++i) {
     x1 *= 64.f;
@@ -650,10 +660,7 @@ __device__ __forceinline__ void tc_slices(float x1, float x2, float (&t)[kTcSlic
   }
 }
 
-// 2^e as a double for -1022 <= e <= 1023 (exact, integer operations only).
-__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
-
-// (lo + s hi) w as an FP32 pair, s = +1 or -1: exact sum, then the product with w1 + w2.
+// (lo + hi) w as an FP32 pair: exact sum, then the product with w1 + w2.
 __device__ __forceinline__ void tc_pair(float lo, float hi, float w1, float w2, float& y1, float& y2) {
   const float s1 = lo + hi;
   const float bb = s1 - lo;
@@ -663,14 +670,36 @@ __device__ __forceinline__ void tc_pair(float lo, float hi, float w1, float w2, 
   y1 = p;
   y2 = e + fmaf(s1, w2, s2 * w1);
 }
+
+// FP64 storage: slices of v with |v| < 2^E from its bit pattern: F = floor(|v| 2^(63-E)) < 2^63,
+// slice i = bits 62-7i .. 56-7i of F (as an exact float, with v's sign).
+__device__ __forceinline__ void tc_slices64(double v, int E, float (&t)[kTcSlices]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int ev = (int)((bits >> 52) & 0x7FFull);
+  unsigned long long F = 0ull;
+  if (ev != 0) {
+    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = (ev - 1075) + 63 - E;
+    if (sh >= 0)
+      F = mant << sh;
+    else if (sh > -64)
+      F = mant >> (-sh);
+  }
+  const unsigned sgn = (unsigned)(bits >> 63) << 31;
+#pragma unroll
+  for (int i = 0; i < kTcSlices; ++i) {
+    const unsigned u = (unsigned)(F >> (56 - 7 * i)) & 0x7Fu;
+    t[i] = __uint_as_float(__float_as_uint(__int_as_float(0x4B000000 | (int)u) - 8388608.f) | sgn);
+  }
+}
 }  // namespace
 
-template <int DPAD>
-__global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateDesc* __restrict__ gates,
+template <typename T, int DPAD>
+__global__ void __launch_bounds__(kTcThreads, 2) k_gram_tc(SweepArgs a, const GateDesc* __restrict__ gates,
                                                         double* __restrict__ gram, int64_t n_jobs, int nchunk,
                                                         int chunk_rows) {
   using Cfg = TcCfg<DPAD>;
-  constexpr int KB = Cfg::KB, NACC = Cfg::NACC, NCOL = Cfg::NCOL;
+  constexpr int KB = Cfg::KB, NACC = Cfg::NACC, NCOL = Cfg::NCOL, BITS = TcBits<T>::BITS;
   constexpr uint32_t IDESC = tc::idesc_bf16(128, 128);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
@@ -679,8 +708,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
   __shared__ int colexp[DPAD];
   __shared__ float colscale[DPAD];
   unsigned char* opnd = smem_raw;
-  float* wt = reinterpret_cast<float*>(smem_raw + tc_operand_bytes<DPAD>());
-  double* lamv = reinterpret_cast<double*>(wt + 2 * KB);
+  double* wt = reinterpret_cast<double*>(smem_raw + tc_operand_bytes<DPAD>());   // [KB] row weights
+  double* lamv = wt + KB;
   double* red = reinterpret_cast<double*>(smem_raw);   // end-of-job reduction (aliases the operands)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int chi = a.chi;
@@ -712,20 +741,20 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
     const int r_end = min(rows, r_begin + chunk_rows);
     const int64_t SZ = (int64_t)OI * D;
     const int inner = sd.inner;
-    const float* gin = reinterpret_cast<const float*>(a.gamma) + (int64_t)jb.b * a.shot_elems + sd.in_off;
-    // 1. column bounds
+    const T* gin = reinterpret_cast<const T*>(a.gamma) + (int64_t)jb.b * a.shot_elems + sd.in_off;
+    // 1. column bounds (the FP32 value of each bound; the exponent below has a bit of margin)
     {
       float cm[DPAD];
 #pragma unroll
       for (int c = 0; c < DPAD; ++c) cm[c] = 0.f;
       for (int r = r_begin + tid; r < r_end; r += kTcThreads) {
         const int pr = r / OI, oi = r % OI, o = oi / inner, i = oi % inner;
-        const float w = (float)row_weight<double>(sd, o, i, lamv, chi);
-        const float* plo = gin + pg.lo(pr) * SZ + (int64_t)o * D * inner + i;
-        const float* phi = gin + pg.hi(pr) * SZ + (int64_t)o * D * inner + i;
+        const T w = T(row_weight<double>(sd, o, i, lamv, chi));
+        const T* plo = gin + pg.lo(pr) * SZ + (int64_t)o * D * inner + i;
+        const T* phi = gin + pg.hi(pr) * SZ + (int64_t)o * D * inner + i;
 #pragma unroll
         for (int c = 0; c < DPAD; ++c)
-          if (c < D) cm[c] = fmaxf(cm[c], (fabsf(plo[(int64_t)c * inner]) + fabsf(phi[(int64_t)c * inner])) * w);
+          if (c < D) cm[c] = fmaxf(cm[c], float((fabs(plo[(int64_t)c * inner]) + fabs(phi[(int64_t)c * inner])) * w));
       }
 #pragma unroll
       for (int c = 0; c < DPAD; ++c) {
@@ -752,7 +781,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
     const int nblk = (r_end - r_begin + KB - 1) / KB;
     for (int blk = 0; blk < nblk; ++blk) {
       const int rb = r_begin + blk * KB;
-      // 2. row weights of the block as FP32 pairs
+      // 2. row weights of the block
       for (int k = tid; k < KB; k += kTcThreads) {
         const int r = rb + k;
         double w = 0.0;
@@ -760,18 +789,16 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
           const int oi = r % OI;
           w = row_weight<double>(sd, oi / inner, oi % inner, lamv, chi);
         }
-        const float w1 = (float)w;
-        wt[2 * k] = w1;
-        wt[2 * k + 1] = (float)(w - (double)w1);
+        wt[k] = w;
       }
       __syncthreads();
       {
-        float lo8[8], hi8[8];
+        T lo8[8], hi8[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int r = rb + kg * 8 + u;
-          lo8[u] = 0.f;
-          hi8[u] = 0.f;
+          lo8[u] = T(0);
+          hi8[u] = T(0);
           if (qi < D && r < r_end) {
             const int pr = r / OI, oi = r % OI, o = oi / inner, i = oi % inner;
             const int64_t off = (int64_t)o * D * inner + (int64_t)qi * inner + i;
@@ -780,18 +807,26 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
           }
         }
         const float sc = colscale[qi];
+        const int E = colexp[qi];
 #pragma unroll
         for (int pt = 0; pt < 2; ++pt) {
           uint32_t pk[kTcSlices][4];
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             float t0[kTcSlices], t1[kTcSlices];
-            float y1, y2;
             const int k0 = kg * 8 + 2 * v;
-            tc_pair(lo8[2 * v], pt ? -hi8[2 * v] : hi8[2 * v], wt[2 * k0], wt[2 * k0 + 1], y1, y2);
-            tc_slices(y1 * sc, y2 * sc, t0);
-            tc_pair(lo8[2 * v + 1], pt ? -hi8[2 * v + 1] : hi8[2 * v + 1], wt[2 * k0 + 2], wt[2 * k0 + 3], y1, y2);
-            tc_slices(y1 * sc, y2 * sc, t1);
+            if constexpr (sizeof(T) == 4) {
+              float y1, y2;
+              const double w0 = wt[k0], w1 = wt[k0 + 1];
+              const float w0a = (float)w0, w1a = (float)w1;
+              tc_pair(lo8[2 * v], pt ? -hi8[2 * v] : hi8[2 * v], w0a, (float)(w0 - (double)w0a), y1, y2);
+              tc_slices32(y1 * sc, y2 * sc, t0);
+              tc_pair(lo8[2 * v + 1], pt ? -hi8[2 * v + 1] : hi8[2 * v + 1], w1a, (float)(w1 - (double)w1a), y1, y2);
+              tc_slices32(y1 * sc, y2 * sc, t1);
+            } else {
+              tc_slices64((pt ? lo8[2 * v] - hi8[2 * v] : lo8[2 * v] + hi8[2 * v]) * wt[k0], E, t0);
+              tc_slices64((pt ? lo8[2 * v + 1] - hi8[2 * v + 1] : lo8[2 * v + 1] + hi8[2 * v + 1]) * wt[k0 + 1], E, t1);
+            }
 #pragma unroll
             for (int i = 0; i < kTcSlices; ++i) {
               const __nv_bfloat162 h = __floats2bfloat162_rn(t0[i], t1[i]);
@@ -841,7 +876,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
           for (int j = 0; j < kTcSlices; ++j) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(sel * 128 + j * 16), v);
-            const double scl = pow2d(-6 * (ia + j + 2));
+            const double scl = pow2d(-BITS * (ia + j + 2));
 #pragma unroll
             for (int c = 0; c < DPAD; ++c) part[c] += (double)v[c] * scl;
           }
@@ -854,7 +889,7 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(pa * 64 + jj * 16), v);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const double scl = pow2d(-6 * (ia + 2 * jj + h + 2));
+              const double scl = pow2d(-BITS * (ia + 2 * jj + h + 2));
 #pragma unroll
               for (int c = 0; c < DPAD; ++c) part[c] += (double)v[h * DPAD + c] * scl;
             }
@@ -894,29 +929,33 @@ __global__ void __launch_bounds__(kTcThreads) k_gram_tc(SweepArgs a, const GateD
   if (warp == 0) tc::tmem_dealloc(tmem, NCOL);
 }
 
-template <int DPAD>
+template <typename T, int DPAD>
 static cudaError_t gram_tc_launch(const SweepArgs& a, const GateDesc* g, int count, double* gram, int nchunk,
                                   int chunk_rows, cudaStream_t st) {
   const int64_t n_jobs = (int64_t)count * a.B * 2 * nchunk;
   if (n_jobs == 0) return cudaSuccess;
   const size_t smem = tc_smem_bytes<DPAD>(a.chi);
-  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<T, DPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(n_jobs, 2LL * nsm);
-  k_gram_tc<DPAD><<<(unsigned)grid, kTcThreads, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
+  k_gram_tc<T, DPAD><<<(unsigned)grid, kTcThreads, smem, st>>>(a, g, gram, n_jobs, nchunk, chunk_rows);
   return cudaGetLastError();
 }
 
 bool gram_tc_supported(int maxD) { return maxD >= 4 && maxD <= 16; }
 
+template <typename T>
 cudaError_t launch_gram_tc(const SweepArgs& a, const GateDesc* g, int count, int maxD, double* gram, int nchunk,
                            int chunk_rows, cudaStream_t st) {
-  return maxD <= 8 ? gram_tc_launch<8>(a, g, count, gram, nchunk, chunk_rows, st)
-                   : gram_tc_launch<16>(a, g, count, gram, nchunk, chunk_rows, st);
+  return maxD <= 8 ? gram_tc_launch<T, 8>(a, g, count, gram, nchunk, chunk_rows, st)
+                   : gram_tc_launch<T, 16>(a, g, count, gram, nchunk, chunk_rows, st);
 }
+template cudaError_t launch_gram_tc<float>(const SweepArgs&, const GateDesc*, int, int, double*, int, int, cudaStream_t);
+template cudaError_t launch_gram_tc<double>(const SweepArgs&, const GateDesc*, int, int, double*, int, int,
+                                            cudaStream_t);
 
 template cudaError_t launch_gram2<float>(const SweepArgs&, const GateDesc*, int, int, double*, int, int, cudaStream_t);
 template cudaError_t launch_gram2<double>(const SweepArgs&, const GateDesc*, int, int, double*, int, int,

@@ -483,7 +483,7 @@ __device__ void gate_bwd(const AdjArgs& a, int b, int g, double* scr, double* gb
                          double* red) {
   const GateDesc& gd = a.gates[g];
   const int D = gd.D, chi = a.chi, bond = gd.bond, L2 = 2 * chi, CC = chi * chi;
-  const double* rec = a.rec_core + ((int64_t)g * a.B + b) * core_rec_elems(chi);
+  const double* rec = a.rec_core + ((int64_t)(g - a.rec_gate0) * a.B + b) * core_rec_elems(chi);
   const int rk[4] = {(int)rec[0], (int)rec[1], (int)rec[2], (int)rec[3]};
   const int k = (int)rec[4];
   const double s0 = rec[5];
@@ -797,7 +797,7 @@ __device__ void local_bwd(const AdjArgs& a, int b, int t, int s, double* gbar, d
   const int P = ld.P, rest = ld.rest;
   const double* gin = a.hist + (int64_t)b * a.hist_elems + ld.off;
   double* gb = gbar + (int64_t)s * a.max_site;
-  const double sc = a.rec_sc[((int64_t)t * a.B + b) * a.S + s];
+  const double sc = a.rec_sc[((int64_t)(t - a.t_begin) * a.B + b) * a.S + s];
   const int m = a.det[(int64_t)(a.wave_first + b) * a.n_det + ld.det] & 1;
   double acc[kMaxPhys * kMaxPhys];
   for (int e = 0; e < P * P; ++e) acc[e] = 0.0;
@@ -837,16 +837,21 @@ __global__ void __launch_bounds__(256, 4) k_adjoint(AdjArgs a) {
   double* Kb = a.Kbar + (int64_t)b * a.T * a.S * 16;
   double* pb = a.pbar + (int64_t)b * a.n_gates;
   double* Rb = a.Rbar + (int64_t)b * a.S * 8;
-  for (int w = threadIdx.x; w < a.T * a.S * 16; w += blockDim.x) Kb[w] = 0.0;
-  for (int w = threadIdx.x; w < a.n_gates; w += blockDim.x) pb[w] = 0.0;
-  for (int w = threadIdx.x; w < a.S * 8; w += blockDim.x) Rb[w] = 0.0;
-  for (int w = threadIdx.x; w < a.nbonds * a.chi; w += blockDim.x) lambar[w] = 0.0;
-  __syncthreads();
+  if (a.do_final) {
+    for (int w = threadIdx.x; w < a.T * a.S * 16; w += blockDim.x) Kb[w] = 0.0;
+    for (int w = threadIdx.x; w < a.n_gates; w += blockDim.x) pb[w] = 0.0;
+    for (int w = threadIdx.x; w < a.S * 8; w += blockDim.x) Rb[w] = 0.0;
+    for (int w = threadIdx.x; w < a.nbonds * a.chi; w += blockDim.x) lambar[w] = 0.0;
+    __syncthreads();
+  }
   const double z = a.Z[2 * b] + a.Z[2 * b + 1];
   if (!(z > 0.0) || !(z < INFINITY)) return;   // probability 0: contributes nothing
-  final_bwd(a, b, scr, gbar, lambar, Rb, red, red2);
-  __syncthreads();
-  for (int t = a.T - 1; t >= 0; --t) {
+  if (a.do_final) {
+    final_bwd(a, b, scr, gbar, lambar, Rb, red, red2);
+    __syncthreads();
+  }
+  // the layers of this segment, backwards (gbar, lambar and lam carry over between segments)
+  for (int t = a.t_end - 1; t >= a.t_begin; --t) {
     for (int rd = a.layer_round[t + 1] - 1; rd >= a.layer_round[t]; --rd)
       for (int g = a.round_first[rd + 1] - 1; g >= a.round_first[rd]; --g) gate_bwd(a, b, g, scr, gbar, lambar, lam, red2);
     for (int s = 0; s < a.S; ++s) local_bwd(a, b, t, s, gbar, red);

@@ -81,6 +81,8 @@ struct td_network {
   td::FinalSite* d_hfinals = nullptr;
   int32_t* d_round_first = nullptr;
   int32_t* d_layer_round = nullptr;
+  int64_t *d_seg_in_off = nullptr, *d_seg_out_off = nullptr, *d_seg_len = nullptr, *d_ckpt_off = nullptr;
+  double* d_ckpt = nullptr;      // [grad_wave][ckpt_shot_elems] checkpointed segment inputs
   int32_t grad_wave = 0;
   int64_t gfscr_elems = 0;      // per-shot elements of d_gfscr as allocated
   double *d_hist = nullptr, *d_rec_core = nullptr, *d_rec_sc = nullptr, *d_rec_fin = nullptr, *d_adj_scr = nullptr,
@@ -227,7 +229,7 @@ void td_default_options(td_options* opt) {
   opt->chi = 8;
   opt->chi_mps = 16;
   opt->precision = TD_FP64;
-  opt->ckpt_stride = 4;
+  opt->ckpt_stride = 0;
   opt->svd_cutoff = 1e-12;
   opt->multiplet_rtol = 1e-8;
   opt->gram_cutoff = -1.0;   // per precision
@@ -260,7 +262,7 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   net->opt = o;
   const int chi = P.chi, cm = P.chi_mps, Dm = P.max_final_D;
   if ((int64_t)cm * Dm > 256) { delete net; return fail(TD_ERR_UNSUPPORTED, "chi_mps * final bond dimension must be <= 256"); }
-  net->elem = (o.precision == TD_FP64) ? 8 : 4;
+  net->elem = (o.precision == TD_FP32) ? 4 : 8;
   net->nslots = P.S + P.n_bonds + 1;
 
   // final-contraction scratch per shot (elements of the accumulation type): the boundary
@@ -367,9 +369,10 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     a.vs = vs;
     a.ovr = ovr;
     a.chunk_rows = net->chunk_rows;
-    a.tc = P.precision == TD_TC ? 1 : 0;
+    a.tc = P.precision == TD_FP64 ? 0 : 1;
+    a.precond = P.precision == TD_FP64 ? 0 : 1;
     a.status = net->d_status;
-    const bool f64 = P.precision == TD_FP64;
+    const bool f64 = P.precision != TD_FP32;   // storage type
     cudaError_t e;
     {
       td_network::Mark mk(net, TD_K_INIT, st);
@@ -433,6 +436,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     z.offset_all = P.offset_all;
     for (int i = 0; i < 4; ++i) z.mix[i] = P.glob_mix[i];
     z.vs = vs;
+    z.status = net->d_status;
     {
       td_network::Mark mk(net, TD_K_FINALIZE, st);
       e = td::launch_finalize(z, st);
@@ -498,9 +502,11 @@ td_status td_network_check(td_network* net, void* stream) {
     return cuda_fail(e, "status read");
   if (code == TD_OK) return TD_OK;
   if ((e = cudaMemset(net->d_status, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "status reset");
-  return fail((td_status)code, code == TD_ERR_TIMEOUT ? "a tensor-core kernel gave up waiting for its MMAs; the "
-                                                        "results of the calls since the last check are not valid"
-                                                      : "a kernel recorded an error status");
+  return fail((td_status)code,
+              code == TD_ERR_TIMEOUT ? "a tensor-core kernel gave up waiting for its MMAs; the results of the calls "
+                                       "since the last check are not valid"
+              : code == TD_ERR_NUMERIC ? "a shot met a non-finite intermediate; its log-probabilities are NaN"
+                                       : "a kernel recorded an error status");
 }
 
 td_status td_coset_logprob_static(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
@@ -728,8 +734,13 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
   G.rec_stride = fin_stride; G.rec_slot = fin_slot;
   G.rec_mC = (int32_t)mC; G.rec_mA = (int32_t)mA; G.rec_m = m_max; G.rec_n = n_max;
   const int64_t n_gates = (int64_t)P.gates.size();
-  const size_t per_shot = 8 * (size_t)(P.hist_shot_elems + n_gates * core_rec + (int64_t)P.T * P.S + fin_stride +
-                                       A.scr_stride + G.scratch_elems + (int64_t)P.T * P.S * 16 + n_gates + P.S * 8 + 2);
+  const int32_t nseg = (int32_t)P.seg_first_layer.size() - 1;
+  int64_t seg_gates = 1;
+  for (int32_t j = 0; j < nseg; ++j) seg_gates = std::max<int64_t>(seg_gates, P.seg_first_gate[j + 1] - P.seg_first_gate[j]);
+  const int64_t seg_layers = P.ckpt_stride;
+  const size_t per_shot = 8 * (size_t)(P.hist_shot_elems + P.ckpt_shot_elems + seg_gates * core_rec + seg_layers * P.S +
+                                       fin_stride + A.scr_stride + G.scratch_elems + (int64_t)P.T * P.S * 16 + n_gates +
+                                       P.S * 8 + 2);
   const size_t budget = net->opt.mem_budget ? net->opt.mem_budget : (size_t(16) << 30);
   int64_t gw = std::min<int64_t>({(int64_t)net->wave, std::max<int64_t>(B, 1),
                                    std::max<int64_t>(1, (int64_t)(budget / std::max<size_t>(per_shot, 1)))});
@@ -738,7 +749,7 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
   if (net->d_hist && gw <= net->grad_wave && G.scratch_elems <= net->gfscr_elems) return TD_OK;
   gw = std::max<int64_t>(gw, net->grad_wave);
   for (double** pp : {&net->d_hist, &net->d_rec_core, &net->d_rec_sc, &net->d_rec_fin, &net->d_adj_scr, &net->d_gfscr,
-                      &net->d_Kbar, &net->d_pbar, &net->d_Rbar, &net->d_glogp})
+                      &net->d_Kbar, &net->d_pbar, &net->d_Rbar, &net->d_glogp, &net->d_ckpt})
     if (*pp) {
       cudaFree(*pp);
       net->allocs.erase(std::remove(net->allocs.begin(), net->allocs.end(), (void*)*pp), net->allocs.end());
@@ -746,8 +757,9 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
     }
   net->grad_wave = 0;
   auto res = [&](double*& ptr, int64_t n) { size_t c = 0; return net->reserve(ptr, c, (size_t)n); };
-  if (!res(net->d_hist, gw * P.hist_shot_elems) || !res(net->d_rec_core, std::max<int64_t>(n_gates, 1) * gw * core_rec) ||
-      !res(net->d_rec_sc, (int64_t)P.T * gw * P.S) || !res(net->d_rec_fin, gw * fin_stride) ||
+  if (!res(net->d_hist, gw * P.hist_shot_elems) || !res(net->d_rec_core, seg_gates * gw * core_rec) ||
+      !res(net->d_ckpt, std::max<int64_t>(gw * P.ckpt_shot_elems, 1)) ||
+      !res(net->d_rec_sc, seg_layers * gw * P.S) || !res(net->d_rec_fin, gw * fin_stride) ||
       !res(net->d_adj_scr, gw * A.scr_stride) || !res(net->d_gfscr, gw * G.scratch_elems) ||
       !res(net->d_Kbar, gw * P.T * P.S * 16) || !res(net->d_pbar, gw * std::max<int64_t>(n_gates, 1)) ||
       !res(net->d_Rbar, gw * P.S * 8) || !res(net->d_glogp, gw * 2))
@@ -761,12 +773,20 @@ static td_status prepare_reverse(td_network* net, int64_t B) {
     }
     lr.push_back(nr);
     rf.push_back((int32_t)P.gates.size());
-    size_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+    size_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0, c7 = 0, c8 = 0, c9 = 0;
+    const size_t nst = P.seg_in_off.size();
     if (!net->reserve(net->d_hgates, c1, std::max<size_t>(P.hist_gates.size(), 1)) ||
         !net->reserve(net->d_hlocals, c2, P.hist_locals.size()) || !net->reserve(net->d_hfinals, c3, P.hist_finals.size()) ||
-        !net->reserve(net->d_round_first, c4, rf.size()) || !net->reserve(net->d_layer_round, c5, lr.size()))
+        !net->reserve(net->d_round_first, c4, rf.size()) || !net->reserve(net->d_layer_round, c5, lr.size()) ||
+        !net->reserve(net->d_seg_in_off, c6, nst) || !net->reserve(net->d_seg_out_off, c7, nst) ||
+        !net->reserve(net->d_seg_len, c8, nst) || !net->reserve(net->d_ckpt_off, c9, nst))
       return fail(TD_ERR_OOM, "reverse-sweep descriptors");
     cudaError_t e;
+    if ((e = cudaMemcpy(net->d_seg_in_off, P.seg_in_off.data(), 8 * nst, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->d_seg_out_off, P.seg_out_off.data(), 8 * nst, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->d_seg_len, P.seg_in_elems.data(), 8 * nst, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->d_ckpt_off, P.ckpt_off.data(), 8 * nst, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "reverse-sweep segment tables");
     if ((!P.hist_gates.empty() && (e = cudaMemcpy(net->d_hgates, P.hist_gates.data(), sizeof(td::GateDesc) * P.hist_gates.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
         (e = cudaMemcpy(net->d_hlocals, P.hist_locals.data(), sizeof(td::LocalDesc) * P.hist_locals.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(net->d_hfinals, P.hist_finals.data(), sizeof(td::FinalSite) * P.hist_finals.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -826,6 +846,7 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
   std::vector<double> Ksum((size_t)T * S * 16, 0.0), psum((size_t)n_gates, 0.0), Rsum((size_t)S * 8, 0.0);
   std::vector<double> hK, hp, hR;
   const int64_t gw = net->grad_wave;
+  const int32_t nseg = (int32_t)P.seg_first_layer.size() - 1;
   for (int64_t w0 = 0; w0 < B; w0 += gw) {
     const int32_t Bw = (int32_t)std::min<int64_t>(gw, B - w0);
     td::SweepArgs a{};
@@ -840,15 +861,50 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
     a.gram_cutoff = P.gram_cutoff; a.svd_cutoff = P.svd_cutoff; a.multiplet_rtol = P.multiplet_rtol;
     a.rec_core = net->d_rec_core;
     a.chunk_rows = net->chunk_rows;
-    if ((e = td::launch_sweep_init<double, double>(a, net->d_hlocals, S, st)) != cudaSuccess) return cuda_fail(e, "init launch");
-    for (int32_t t = 0; t < T; ++t) {
-      a.layer = t;
-      a.rec_sc = net->d_rec_sc + (int64_t)t * Bw * S;
-      if ((e = td::launch_local<double, double>(a, net->d_hlocals + (int64_t)t * S, S, st)) != cudaSuccess)
-        return cuda_fail(e, "local launch");
-      for (const td::Round& rd : P.layers[t].rounds)
-        if ((e = td::launch_round<double, double>(a, net->d_hgates, rd, net->d_gram, net->d_tbuf, S, st)) != cudaSuccess)
-          return cuda_fail(e, "gate round launch");
+    a.status = net->d_status;
+    const int64_t lam_elems = (int64_t)P.n_bonds * chi, lam_stride = lam_elems;
+    // forward sweep of segment j in the versioned layout, recording its cores and scales;
+    // a segment j >= 1 starts from its checkpoint (tensors and bond weights), segment 0
+    // from the product state
+    auto forward_segment = [&](int32_t j) -> td_status {
+      cudaError_t e2;
+      if (j == 0) {
+        if ((e2 = td::launch_sweep_init<double, double>(a, net->d_hlocals, S, st)) != cudaSuccess)
+          return cuda_fail(e2, "init launch");
+      } else {
+        if ((e2 = td::launch_copy_sites(net->d_ckpt, P.ckpt_shot_elems, net->d_ckpt_off + (size_t)j * S, net->d_hist,
+                                        P.hist_shot_elems, net->d_seg_in_off + (size_t)j * S,
+                                        net->d_seg_len + (size_t)j * S, S, Bw, st)) != cudaSuccess ||
+            (e2 = td::launch_copy_rows(net->d_ckpt, P.ckpt_shot_elems, P.ckpt_lam_off[j], net->d_lam, lam_stride, 0,
+                                       lam_elems, Bw, st)) != cudaSuccess)
+          return cuda_fail(e2, "checkpoint restore");
+      }
+      const int32_t t0 = P.seg_first_layer[j], t1 = P.seg_first_layer[j + 1];
+      a.rec_gate0 = P.seg_first_gate[j];
+      for (int32_t t = t0; t < t1; ++t) {
+        a.layer = t;
+        a.rec_sc = net->d_rec_sc + (int64_t)(t - t0) * Bw * S;
+        if ((e2 = td::launch_local<double, double>(a, net->d_hlocals + (int64_t)t * S, S, st)) != cudaSuccess)
+          return cuda_fail(e2, "local launch");
+        for (const td::Round& rd : P.layers[t].rounds)
+          if ((e2 = td::launch_round<double, double>(a, net->d_hgates, rd, net->d_gram, net->d_tbuf, S, st)) != cudaSuccess)
+            return cuda_fail(e2, "gate round launch");
+      }
+      return TD_OK;
+    };
+    cudaError_t e;
+    for (int32_t j = 0; j < nseg; ++j) {
+      if (j > 0) {
+        // checkpoint: the previous segment's output tensors and the bond weights
+        if ((e = td::launch_copy_sites(net->d_hist, P.hist_shot_elems, net->d_seg_out_off + (size_t)(j - 1) * S,
+                                       net->d_ckpt, P.ckpt_shot_elems, net->d_ckpt_off + (size_t)j * S,
+                                       net->d_seg_len + (size_t)j * S, S, Bw, st)) != cudaSuccess ||
+            (e = td::launch_copy_rows(net->d_lam, lam_stride, 0, net->d_ckpt, P.ckpt_shot_elems, P.ckpt_lam_off[j],
+                                      lam_elems, Bw, st)) != cudaSuccess)
+          return cuda_fail(e, "checkpoint save");
+      }
+      s = forward_segment(j);
+      if (s != TD_OK) return s;
     }
     td::FinalArgs f = net->gfin;
     f.gamma = net->d_hist; f.shot_elems = P.hist_shot_elems; f.lam = net->d_lam; f.logacc = net->d_logacc;
@@ -877,7 +933,19 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
     A.S = S; A.T = T; A.nbonds = P.n_bonds; A.chi = chi; A.nx = P.nx; A.ny = P.ny; A.B = Bw;
     A.n_gates = (int32_t)n_gates; A.max_final_D = P.max_final_D; A.mps_stride = (int32_t)net->fin.mps_stride;
     A.Kbar = net->d_Kbar; A.pbar = net->d_pbar; A.Rbar = net->d_Rbar;
-    if ((e = td::launch_adjoint(A, 256, st)) != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    // reverse sweep, one segment at a time from the last: the last segment's record is in
+    // place; every earlier one is recomputed from its checkpoint first
+    for (int32_t j = nseg - 1; j >= 0; --j) {
+      if (j < nseg - 1) {
+        s = forward_segment(j);
+        if (s != TD_OK) return s;
+      }
+      A.t_begin = P.seg_first_layer[j];
+      A.t_end = P.seg_first_layer[j + 1];
+      A.rec_gate0 = P.seg_first_gate[j];
+      A.do_final = (j == nseg - 1) ? 1 : 0;
+      if ((e = td::launch_adjoint(A, 256, st)) != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    }
     hK.resize((size_t)Bw * T * S * 16); hp.resize((size_t)Bw * n_gates); hR.resize((size_t)Bw * S * 8);
     if ((e = cudaMemcpyAsync(hK.data(), net->d_Kbar, sizeof(double) * hK.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (n_gates > 0 && (e = cudaMemcpyAsync(hp.data(), net->d_pbar, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
@@ -1009,7 +1077,10 @@ td_status td_debug_sweep(td_network* net, const uint8_t* det_dev, int64_t B, int
   a.det = det_dev; a.nbonds = P.n_bonds; a.chi = P.chi; a.nslots = net->nslots; a.n_det = P.n_det;
   a.wave_first = 0; a.B = Bw;
   a.gram_cutoff = P.gram_cutoff; a.svd_cutoff = P.svd_cutoff; a.multiplet_rtol = P.multiplet_rtol;
-  const bool f64 = P.precision == TD_FP64;
+  a.tc = P.precision == TD_FP64 ? 0 : 1;
+  a.precond = P.precision == TD_FP64 ? 0 : 1;
+  a.status = net->d_status;
+  const bool f64 = P.precision != TD_FP32;   // storage type
   cudaError_t e = f64 ? td::launch_sweep_init<double, double>(a, net->d_locals, P.S, st)
                       : td::launch_sweep_init<float, float>(a, net->d_locals, P.S, st);
   if (e != cudaSuccess) return cuda_fail(e, "init launch");
@@ -1060,7 +1131,7 @@ td_status td_network_get_work(const td_network* net, double* bytes, double* flop
   if (!net || !bytes || !flops || !fp64_flops) return fail(TD_ERR_INVALID, "null argument");
   const td::Plan& P = net->plan;
   const double el = (double)net->elem;
-  const bool f64 = P.precision == TD_FP64;
+  const bool f64 = P.precision == TD_FP64;   // the update in FP64 arithmetic on FP64 storage only counts as FP64 work
   for (int k = 0; k < TD_K_COUNT; ++k) { bytes[k] = 0; flops[k] = 0; fp64_flops[k] = 0; }
   auto eig = [](double n) { return 9.0 * n * n * n; };
   auto svd = [](double m, double n) {

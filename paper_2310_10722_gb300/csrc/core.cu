@@ -121,7 +121,8 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
   const int rAp = rk[0], rA = rk[0] + rk[1], rBp = rk[2], rB = rk[2] + rk[3];
   double* tout = tbuf + item * 4 * chi * chi;
   // record for the reverse sweep: ranks, old lambda, R factors and right inverses
-  double* rec = a.rec_core ? a.rec_core + ((int64_t)(a.gate_base + gi) * a.B + b) * core_rec_elems(chi) : nullptr;
+  double* rec = a.rec_core ? a.rec_core + ((int64_t)(a.gate_base + gi - a.rec_gate0) * a.B + b) * core_rec_elems(chi)
+                           : nullptr;
   const int CC = chi * chi, L2 = 2 * chi;
   if (rec) {
     if (tm.tid < 4) rec[tm.tid] = rk[tm.tid];

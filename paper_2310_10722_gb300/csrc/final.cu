@@ -18,8 +18,10 @@
 // of the m x m factor R (half-length columns; R V has orthogonal columns exactly when M^T V
 // has).  The carry is then (M^T V_k)^T from the unreduced M^T.  On the mixed path the
 // Jacobi of R is preconditioned by an FP32 solve and finished by FP64 sweeps run to
-// convergence (svd_precond).  The gradient pass's recorded forward keeps the unreduced
-// Jacobi on M^T (its records are M^T V and V).
+// convergence (svd_precond), and only for the chi_mps + 2 columns of largest norm, the only
+// ones a cut can keep (and the one after them, for the multiplet rule): the FP64 sweeps rotate
+// just the pairs that involve one of them.  The gradient pass's recorded forward keeps the
+// unreduced Jacobi on M^T (its records are M^T V and V).
 #include <cmath>
 #include <mutex>
 
@@ -205,7 +207,8 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
           tm.sync();
           if constexpr (sizeof(R) == 8) {
             if (fa.precond)
-              svd_precond(tm, Rk, ldr, m, m, V, ldvv, work + fa.w_P, work + fa.w_T, meta + 7, &slot_s);
+              svd_precond(tm, Rk, ldr, m, m, V, ldvv, work + fa.w_P, work + fa.w_T, meta + 7, &slot_s,
+                          fa.chi_mps + 2 < m ? fa.chi_mps + 2 : 0, sv, ord);
             else
               team_svd_onesided<R>(tm, Rk, ldr, m, m, V, ldvv, meta + 7, 40, true);
           } else {
@@ -369,6 +372,12 @@ __global__ void k_finalize(FinalizeArgs f) {
   for (int c = 0; c < 2; ++c) {
     const double z = zz[c ^ off];
     lp[c] = (z > 0.0 && ls > -INFINITY) ? log(z) + ls : -INFINITY;
+  }
+  // a non-finite intermediate (NaN in a log-scale or in the final contraction, or an
+  // infinite weight) makes the shot's result NaN and is reported by td_network_check
+  if (isnan(ls) || isnan(z0) || isnan(z1) || ls == INFINITY || isinf(z0) || isinf(z1)) {
+    lp[0] = lp[1] = NAN;
+    if (f.status) atomicExch(f.status, (int)TD_ERR_NUMERIC);
   }
   const int64_t gb = f.wave_first + b;
   if (f.logp) {

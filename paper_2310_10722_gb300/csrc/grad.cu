@@ -47,4 +47,39 @@ cudaError_t launch_grad_combine(const double* vlogp, int64_t B, int32_t NV, cons
   return cudaGetLastError();
 }
 
+// Checkpoints of the reverse sweep: copies, for every shot b and site s, len[s] doubles from
+// src + b * src_stride + src_off[s] to dst + b * dst_stride + dst_off[s] (the tables in device
+// memory, [S] each).  One block per (site, shot).
+__global__ void k_copy_sites(const double* __restrict__ src, int64_t src_stride, const int64_t* __restrict__ src_off,
+                             double* __restrict__ dst, int64_t dst_stride, const int64_t* __restrict__ dst_off,
+                             const int64_t* __restrict__ len) {
+  const int s = blockIdx.x, b = blockIdx.y;
+  const double* a = src + (int64_t)b * src_stride + src_off[s];
+  double* c = dst + (int64_t)b * dst_stride + dst_off[s];
+  for (int64_t i = threadIdx.x; i < len[s]; i += blockDim.x) c[i] = a[i];
+}
+
+// For every shot b, n doubles from src + b * src_stride + src_off to dst + b * dst_stride + dst_off.
+__global__ void k_copy_rows(const double* __restrict__ src, int64_t src_stride, int64_t src_off,
+                            double* __restrict__ dst, int64_t dst_stride, int64_t dst_off, int64_t n) {
+  const int b = blockIdx.x;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) dst[(int64_t)b * dst_stride + dst_off + i] =
+      src[(int64_t)b * src_stride + src_off + i];
+}
+
+cudaError_t launch_copy_sites(const double* src, int64_t src_stride, const int64_t* src_off, double* dst,
+                              int64_t dst_stride, const int64_t* dst_off, const int64_t* len, int S, int B,
+                              cudaStream_t st) {
+  if (S <= 0 || B <= 0) return cudaSuccess;
+  k_copy_sites<<<dim3(S, B), 256, 0, st>>>(src, src_stride, src_off, dst, dst_stride, dst_off, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_rows(const double* src, int64_t src_stride, int64_t src_off, double* dst, int64_t dst_stride,
+                             int64_t dst_off, int64_t n, int B, cudaStream_t st) {
+  if (n <= 0 || B <= 0) return cudaSuccess;
+  k_copy_rows<<<B, 256, 0, st>>>(src, src_stride, src_off, dst, dst_stride, dst_off, n);
+  return cudaGetLastError();
+}
+
 }  // namespace td

@@ -398,43 +398,79 @@ td_status build_plan(const td_dem& dem, const td_layout& layout, const td_option
   plan.final_dims = dims;
   for (int32_t d : dims) plan.max_final_D = std::max(plan.max_final_D, d);
 
-  // versioned layout: every local operator and gate output gets a new slot
+  // versioned layout of the reverse sweep, one segment of ckpt_stride layers at a time: every
+  // site-local operator and gate output gets a new slot, the slots of a segment start at 0
+  // with the segment's input versions; the tensors at the start of every segment but the first
+  // are kept in a checkpoint area (with the bond weights), the segment is recomputed from it
   {
-    int64_t hacc = 0;
-    auto slot = [&](int64_t n) { int64_t r = hacc; hacc += (n + 3) / 4 * 4; return r; };
-    std::vector<int64_t> ver(S);
-    std::vector<int32_t> hd(plan.n_bonds, 1);
-    for (int32_t s = 0; s < S; ++s) ver[s] = slot(site_size(s, hd));
+    const int32_t k = opt.ckpt_stride >= 1 ? std::min(opt.ckpt_stride, T) : T;
+    plan.ckpt_stride = k;
+    plan.seg_first_layer.clear();
+    plan.seg_first_gate.clear();
+    for (int32_t t = 0; t < T; t += k) plan.seg_first_layer.push_back(t);
+    const int32_t nseg = (int32_t)plan.seg_first_layer.size();
+    plan.seg_first_layer.push_back(T);
+    plan.seg_in_off.assign((size_t)nseg * S, 0);
+    plan.seg_out_off.assign((size_t)nseg * S, 0);
+    plan.seg_in_elems.assign((size_t)nseg * S, 0);
+    plan.ckpt_off.assign((size_t)nseg * S, 0);
+    plan.ckpt_lam_off.assign(nseg, 0);
     plan.hist_locals.clear();
     plan.hist_gates.clear();
+    std::vector<int32_t> hd(plan.n_bonds, 1);
+    std::vector<int64_t> ver(S);
+    int64_t hmax = 0, cacc = 0;
     size_t gi = 0;
-    for (int32_t t = 0; t < T; ++t) {
-      for (int32_t s = 0; s < S; ++s) {
-        LocalDesc ld = plan.locals[(size_t)t * S + s];
-        ld.off = ver[s];
-        ld.out_off = slot(site_size(s, hd));
-        ver[s] = ld.out_off;
-        plan.hist_locals.push_back(ld);
-      }
-      for (const Round& R : plan.layers[t].rounds)
-        for (int32_t q = 0; q < R.count; ++q, ++gi) {
-          GateDesc g = plan.gates[gi];
-          const int32_t ends[2] = {g.side[0].site, g.side[1].site};
-          hd[g.bond] = g.Dn;
-          for (int side = 0; side < 2; ++side) {
-            SideDesc& sd = g.side[side];
-            sd.in_off = ver[ends[side]];
-            sd.out_off = slot(site_size(ends[side], hd));
-            ver[ends[side]] = sd.out_off;
-          }
-          plan.hist_gates.push_back(g);
+    for (int32_t j = 0; j < nseg; ++j) {
+      int64_t hacc = 0;
+      auto slot = [&](int64_t n) { int64_t r = hacc; hacc += (n + 3) / 4 * 4; return r; };
+      plan.seg_first_gate.push_back((int32_t)gi);
+      for (int32_t s2 = 0; s2 < S; ++s2) {
+        const int64_t n = site_size(s2, hd);
+        ver[s2] = slot(n);
+        plan.seg_in_off[(size_t)j * S + s2] = ver[s2];
+        plan.seg_in_elems[(size_t)j * S + s2] = n;
+        if (j > 0) {
+          plan.ckpt_off[(size_t)j * S + s2] = cacc;
+          cacc += (n + 3) / 4 * 4;
         }
+      }
+      if (j > 0) {
+        plan.ckpt_lam_off[j] = cacc;
+        cacc += (int64_t)plan.n_bonds * plan.chi;
+      }
+      for (int32_t t = plan.seg_first_layer[j]; t < plan.seg_first_layer[j + 1]; ++t) {
+        for (int32_t s2 = 0; s2 < S; ++s2) {
+          LocalDesc ld = plan.locals[(size_t)t * S + s2];
+          ld.off = ver[s2];
+          ld.out_off = slot(site_size(s2, hd));
+          ver[s2] = ld.out_off;
+          plan.hist_locals.push_back(ld);
+        }
+        for (const Round& R : plan.layers[t].rounds)
+          for (int32_t q = 0; q < R.count; ++q, ++gi) {
+            GateDesc g = plan.gates[gi];
+            const int32_t ends[2] = {g.side[0].site, g.side[1].site};
+            hd[g.bond] = g.Dn;
+            for (int side = 0; side < 2; ++side) {
+              SideDesc& sd = g.side[side];
+              sd.in_off = ver[ends[side]];
+              sd.out_off = slot(site_size(ends[side], hd));
+              ver[ends[side]] = sd.out_off;
+            }
+            plan.hist_gates.push_back(g);
+          }
+      }
+      for (int32_t s2 = 0; s2 < S; ++s2) plan.seg_out_off[(size_t)j * S + s2] = ver[s2];
+      hmax = std::max(hmax, hacc);
     }
+    plan.seg_first_gate.push_back((int32_t)gi);
     plan.hist_finals = plan.finals;
-    for (int32_t s = 0; s < S; ++s) plan.hist_finals[s].off = ver[s];
-    plan.hist_shot_elems = hacc;
+    for (int32_t s2 = 0; s2 < S; ++s2) plan.hist_finals[s2].off = ver[s2];
+    plan.hist_shot_elems = hmax;
+    plan.ckpt_shot_elems = cacc;
     plan.max_site_elems = 1;
-    for (int32_t s = 0; s < S; ++s) plan.max_site_elems = std::max(plan.max_site_elems, maxsize[s]);
+    for (int32_t s2 = 0; s2 < S; ++s2) plan.max_site_elems = std::max(plan.max_site_elems, maxsize[s2]);
   }
   return TD_OK;
 }

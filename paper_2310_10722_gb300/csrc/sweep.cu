@@ -125,13 +125,13 @@ cudaError_t launch_round(const SweepArgs& a0, const GateDesc* gates, const Round
   auto B = [&](int k) { if (prof) prof->begin(k); };
   auto E = [&](int k) { if (prof) prof->end(k); };
   B(TD_K_GRAM);
-  cudaError_t e = (sizeof(T) == 4 && a.tc && gram_tc_supported(rd.maxD))
-                      ? launch_gram_tc(a, g, rd.count, rd.maxD, gram, a.gram_chunks, cr, st)
+  cudaError_t e = (a.tc && gram_tc_supported(rd.maxD))
+                      ? launch_gram_tc<T>(a, g, rd.count, rd.maxD, gram, a.gram_chunks, cr, st)
                       : launch_gram2<T>(a, g, rd.count, D, gram, a.gram_chunks, cr, st);
   E(TD_K_GRAM);
   if (e != cudaSuccess) return e;
   B(TD_K_CORE);
-  e = launch_core2<R>(a, g, rd.count, rd.maxD, gram, tbuf, S, /*precond=*/sizeof(T) == 4, st);
+  e = launch_core2<R>(a, g, rd.count, rd.maxD, gram, tbuf, S, a.precond != 0, st);
   E(TD_K_CORE);
   if (e != cudaSuccess) return e;
   B(TD_K_UPDATE);

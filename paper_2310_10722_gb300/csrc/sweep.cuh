@@ -27,8 +27,10 @@ struct SweepArgs {
   int32_t gate_base;        // global index of the round's first gate (core)
   // recording for the reverse sweep (null otherwise)
   double* rec_sc;           // [B][S] scale of this layer's site-local operators
-  double* rec_core;         // [gates][B][kCoreRec(chi)] truncation cores (indexed by global gate)
-  int32_t tc;               // Gram pass on the tensor cores (FP32 storage, TD_TC)
+  double* rec_core;         // [gates][B][kCoreRec(chi)] truncation cores (global gate - rec_gate0)
+  int32_t rec_gate0;        // first gate of the recorded segment
+  int32_t tc;               // Gram pass on the tensor cores (TD_FP32, TD_TC)
+  int32_t precond;          // truncation cores: FP32-preconditioned FP64 Jacobi (TD_FP32, TD_TC)
   int* status;              // device status word: a kernel that gives up writes its td_status
 };
 
@@ -99,8 +101,8 @@ struct AdjArgs {
   int64_t hist_elems;
   double* lam;                 // [B][nbonds][chi] lambda after the sweep (restored backwards)
   const double* Z;             // [B][2] final contraction values
-  const double* rec_core;      // [n_gates][B][core_rec_elems(chi)]
-  const double* rec_sc;        // [T][B][S] scales of the site-local operators
+  const double* rec_core;      // [segment gates][B][core_rec_elems(chi)] (gate - rec_gate0)
+  const double* rec_sc;        // [segment layers][B][S] scales of the site-local operators (layer - t_begin)
   const double* rec_fin;       // [B][fin_stride] final-contraction record
   int64_t fin_stride, fin_slot;
   int32_t fin_mC, fin_mA, fin_m, fin_n;
@@ -119,6 +121,9 @@ struct AdjArgs {
   int64_t fo_F, fo_Fb, fo_T1, fo_T1b, fo_M, fo_Mb, fo_C0, fo_C1, fo_A0, fo_A1, fo_Ub, fo_W, fo_J, fo_In, fo_wg,
       fo_off;                  // final-contraction scratch
   int32_t S, T, nbonds, chi, nx, ny, B, n_gates, max_final_D, mps_stride;
+  int32_t t_begin, t_end;      // layers walked by this launch (backwards), a segment of the sweep
+  int32_t rec_gate0;           // first gate of the segment (rec_core index origin)
+  int32_t do_final;            // this launch starts the reverse sweep: adjoint of the final contraction
   double* Kbar;                // [B][T * S][16]
   double* pbar;                // [B][n_gates]
   double* Rbar;                // [B][S][8]
@@ -140,6 +145,7 @@ struct FinalizeArgs {
   int32_t nslots, n_det, wave_first, B, offset_all;
   double mix[4];
   const VShot* vs;           // gradient pass (null otherwise)
+  int* status;               // device status word (TD_ERR_NUMERIC for a non-finite shot), or null
 };
 
 // Optional timing hooks around each kernel launch (kernel class ids of td_kernel_class).
@@ -164,6 +170,13 @@ cudaError_t launch_finalize(const FinalizeArgs& f, cudaStream_t st);
 cudaError_t launch_grad_combine(const double* vlogp, int64_t B, int32_t NV, const int32_t* act, int32_t n_mech,
                                 double* logP, double* grad, cudaStream_t st);
 
+// Checkpoint copies of the reverse sweep (grad.cu).
+cudaError_t launch_copy_sites(const double* src, int64_t src_stride, const int64_t* src_off, double* dst,
+                              int64_t dst_stride, const int64_t* dst_off, const int64_t* len, int S, int B,
+                              cudaStream_t st);
+cudaError_t launch_copy_rows(const double* src, int64_t src_stride, int64_t src_off, double* dst, int64_t dst_stride,
+                             int64_t dst_off, int64_t n, int B, cudaStream_t st);
+
 // Truncation core (core.cu): the simple-update core of every gate of a round; Dm = the
 // round's largest active bond dimension; gram: FP64 partial Grams.
 template <typename R>
@@ -179,8 +192,9 @@ int absorb_chunks(int max_rows, int chunk_rows);
 template <typename T>
 cudaError_t launch_gram2(const SweepArgs& a, const GateDesc* g, int count, int Dm, double* gram, int nchunk,
                          int chunk_rows, cudaStream_t st);
-// Tensor-core Gram (absorb.cu; FP32 storage, bond dimensions 4..16).
+// Tensor-core Gram (absorb.cu; bond dimensions 4..16; T: storage type).
 bool gram_tc_supported(int maxD);
+template <typename T>
 cudaError_t launch_gram_tc(const SweepArgs& a, const GateDesc* g, int count, int maxD, double* gram, int nchunk,
                            int chunk_rows, cudaStream_t st);
 template <typename T>

@@ -120,11 +120,23 @@ struct Plan {
   int32_t max_final_D = 1;               // largest bond after the sweep
   // Versioned layout of the reverse sweep: the same schedule with every site-local
   // operator and every gate writing a new copy of its site tensors, so that every
-  // intermediate tensor of the forward sweep is kept (hist_shot_elems per shot).
+  // intermediate tensor of one segment of ckpt_stride layers is kept (hist_shot_elems per
+  // shot: the largest segment).  Offsets are relative to the segment, whose first slots hold
+  // its input versions; the input tensors of segments 1.. are checkpointed (ckpt_off, with
+  // the bond weights at ckpt_lam_off; ckpt_shot_elems per shot) and the segment recomputed.
   std::vector<LocalDesc> hist_locals;    // off = input version, out_off = output version
   std::vector<GateDesc> hist_gates;      // in_off / out_off = versions
-  std::vector<FinalSite> hist_finals;    // off = last version
+  std::vector<FinalSite> hist_finals;    // off = last version (in the last segment)
   int64_t hist_shot_elems = 0;
+  int32_t ckpt_stride = 1;
+  std::vector<int32_t> seg_first_layer;  // [nseg + 1]
+  std::vector<int32_t> seg_first_gate;   // [nseg + 1]
+  std::vector<int64_t> seg_in_off;       // [nseg][S] input versions of the segment
+  std::vector<int64_t> seg_out_off;      // [nseg][S] output versions of the segment
+  std::vector<int64_t> seg_in_elems;     // [nseg][S] sizes of the input versions
+  std::vector<int64_t> ckpt_off;         // [nseg][S] checkpointed input tensors (segments >= 1)
+  std::vector<int64_t> ckpt_lam_off;     // [nseg] checkpointed bond weights (segments >= 1)
+  int64_t ckpt_shot_elems = 0;
   int64_t max_site_elems = 0;            // largest site tensor of the sweep (elements)
 };
 

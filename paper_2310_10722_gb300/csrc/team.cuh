@@ -403,6 +403,83 @@ __device__ __forceinline__ int team_keep_count(const R* s, int n, int chi, doubl
   return k;
 }
 
+// FP64 (or FP32) one-sided Jacobi sweeps restricted to the column pairs that involve one of
+// the first ktop columns of A (m x n, column-major, lda), V (n x n, ldv) rotated alongside;
+// sweeps until one passes without a rotation.  In step k of the round-robin ordering each of
+// the first ktop columns x meets one partner (k for the fixed player, the fixed player for k,
+// 2k - x mod (ne - 1) otherwise); the pair is handled by the g-lane group of its smaller top
+// member, so each step has at most ktop pairs and every group gets nt / ktop lanes.  On
+// return the first ktop columns are orthogonal to each other and to every other column (the
+// others keep whatever mutual orthogonality they had).  Returns the number of sweeps.
+template <typename R>
+__device__ int team_jacobi_topk(const Team& tm, R* A, int lda, int m, int n, R* V, int ldv, int ktop, int* flag,
+                                int max_sweeps) {
+  tm.sync();
+  if (n < 2 || ktop < 1) return 0;
+  if (ktop > n) ktop = n;
+  const R tol = TeamTol<R>::rel();
+  const int ne = n + (n & 1), mm = ne - 1;
+  int g = tm.nt / ktop;
+  g = g < 1 ? 1 : (g > 32 ? 32 : team_pow2_floor(g));
+  const int rows_max = m > n ? m : n;
+  while (g > 1 && g > rows_max) g >>= 1;
+  const int ngroups = tm.nt / g;
+  const int grp = tm.tid / g, gl = tm.tid % g;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tm.tid == 0) *flag = 0;
+    tm.sync();
+    for (int k = 0; k < ne - 1; ++k) {
+      for (int x0 = 0; x0 < ktop; x0 += ngroups) {
+        const int x = x0 + grp;
+        int y = -1;
+        if (x < ktop) {
+          y = (x == mm) ? k : (x == k ? mm : (2 * k - x + 2 * mm) % mm);
+          if ((y < ktop && y < x) || y >= n) y = -1;
+        }
+        const bool active = y >= 0;
+        const int p = active ? (x < y ? x : y) : 0, q = active ? (x < y ? y : x) : 0;
+        R* ap_ = A + (size_t)p * lda;
+        R* aq_ = A + (size_t)q * lda;
+        R al = R(0), be = R(0), ga = R(0);
+        if (active)
+          for (int r = gl; r < m; r += g) {
+            const R ap = ap_[r], aq = aq_[r];
+            al += ap * ap;
+            be += aq * aq;
+            ga += ap * aq;
+          }
+        for (int o = g >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        R c, s;
+        if (active && jacobi_rot(al, be, ga, tol, c, s)) {
+          if (gl == 0) *flag = 1;
+          for (int r = gl; r < m; r += g) {
+            const R ap = ap_[r], aq = aq_[r];
+            ap_[r] = c * ap - s * aq;
+            aq_[r] = s * ap + c * aq;
+          }
+          R* vp_ = V + (size_t)p * ldv;
+          R* vq_ = V + (size_t)q * ldv;
+          for (int r = gl; r < n; r += g) {
+            const R vp = vp_[r], vq = vq_[r];
+            vp_[r] = c * vp - s * vq;
+            vq_[r] = s * vp + c * vq;
+          }
+        }
+      }
+      tm.sync();
+    }
+    const int any = *flag;
+    tm.sync();
+    if (!any) break;
+  }
+  return sweep;
+}
+
 // Max |x| over the m x n column-major matrix x (ld), through a shared double slot.
 __device__ inline double team_absmax(const Team& tm, const double* x, int ld, int m, int n, double* slot) {
   double v = 0.0;
@@ -441,8 +518,15 @@ __device__ __forceinline__ void team_gemm(const Team& tm, const R* A, int lda, c
 // largest, so the FP64 sweeps are never cut short.  V column-major (ldv).  F: scratch of
 // >= max(m, n) * (max(m, n) + 1) doubles (it also holds the two FP32 matrices); Tt: >= n*n
 // doubles; flag: one team-shared int; slot: one team-shared double.
+// With 0 < ktop < n only the ktop columns of largest norm after the FP32 start are needed to
+// FP64 accuracy (a truncation keeps at most ktop - 2 of them): the columns of A and V are
+// reordered by decreasing norm (nrm: n doubles, ord: n ints of scratch) and the FP64 sweeps
+// rotate only pairs that involve one of the first ktop columns (team_jacobi_topk).  Those
+// columns come out orthogonal to every column; the others, mutually orthogonal to FP32
+// accuracy, give the remaining singular values to FP32 relative accuracy.
 __device__ inline void svd_precond(const Team& tm, double* A, int lda, int m, int n, double* V, int ldv, double* F,
-                            double* Tt, int* flag, double* slot) {
+                                   double* Tt, int* flag, double* slot, int ktop = 0, double* nrm = nullptr,
+                                   int* ord = nullptr) {
   const double amax = team_absmax(tm, A, lda, m, n, slot);
   if (!(amax > 0.0) || n < 2) {
     team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, true);
@@ -491,6 +575,17 @@ __device__ inline void svd_precond(const Team& tm, double* A, int lda, int m, in
   }
   tm.sync();
   for (int w = tm.tid; w < m * n; w += tm.nt) A[(w / m) * lda + (w % m)] = F[w];
+  if (ktop > 0 && ktop < n && nrm && ord) {
+    team_col_norms<double>(tm, A, lda, m, n, nrm);
+    team_sort_desc<double>(tm, nrm, n, ord);
+    for (int w = tm.tid; w < m * n; w += tm.nt) F[w] = A[ord[w / m] * lda + (w % m)];
+    for (int w = tm.tid; w < n * n; w += tm.nt) Tt[w] = V[ord[w / n] * ldv + (w % n)];
+    tm.sync();
+    for (int w = tm.tid; w < m * n; w += tm.nt) A[(w / m) * lda + (w % m)] = F[w];
+    for (int w = tm.tid; w < n * n; w += tm.nt) V[(w / n) * ldv + (w % n)] = Tt[w];
+    team_jacobi_topk<double>(tm, A, lda, m, n, V, ldv, ktop, flag, 40);
+    return;
+  }
   team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, false);
 }
 

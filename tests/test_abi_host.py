@@ -100,3 +100,17 @@ def test_null_network_calls(lib):
     assert lib.td_coset_logprob(None, None, 0, None, None) == 1
     assert lib.td_grad_logprob(None, None, 0, None, None, None, None) == 1
     lib.td_free_network(None)
+
+
+def test_budget_below_one_shot_is_out_of_memory(lib):
+    """A device-memory budget too small for one shot's workspace is refused with TD_ERR_OOM
+    before any allocation (the host-side allocation failure of the build)."""
+    dem = point_sector_3d(3, 0.05)
+    st, msg = _build(lib, dem, mem_budget=1024)
+    assert st == 3 and "mem_budget" in msg, (st, msg)
+
+
+def test_unknown_precision_and_check_without_network(lib):
+    dem = point_sector_3d(3, 0.05)
+    assert _build(lib, dem, precision=3)[0] == 1
+    assert lib.td_network_check(None, None) == 1
