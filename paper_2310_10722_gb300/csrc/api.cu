@@ -251,7 +251,7 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   td_status st = td::build_plan(*dem, *layout, o, net->plan, err);
   if (st != TD_OK) { delete net; return fail(st, err); }
   td::Plan& P = net->plan;
-  if (P.nx > 32) { delete net; return fail(TD_ERR_UNSUPPORTED, "grid wider than 32 sites"); }
+  if (P.nx > td::kMaxGridX) { delete net; return fail(TD_ERR_UNSUPPORTED, "grid wider than 64 sites"); }
   net->H_indptr.assign(dem->H_indptr, dem->H_indptr + dem->n_det + 1);
   net->H_indices.assign(dem->H_indices, dem->H_indices + dem->H_indptr[dem->n_det]);
   net->L_indptr.assign(dem->L_indptr, dem->L_indptr + dem->n_obs + 1);
@@ -261,7 +261,10 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   net->n_obs = dem->n_obs;
   net->opt = o;
   const int chi = P.chi, cm = P.chi_mps, Dm = P.max_final_D;
-  if ((int64_t)cm * Dm > 256) { delete net; return fail(TD_ERR_UNSUPPORTED, "chi_mps * final bond dimension must be <= 256"); }
+  if ((int64_t)cm * Dm > td::kMaxFinalBond) {
+    delete net;
+    return fail(TD_ERR_UNSUPPORTED, "chi_mps * final bond dimension must be <= 1024");
+  }
   net->elem = (o.precision == TD_FP32) ? 4 : 8;
   net->nslots = P.S + P.n_bonds + 1;
 

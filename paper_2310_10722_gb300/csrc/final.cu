@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
   R* Cb[2] = {work + fa.w_C0, work + fa.w_C1};
   R* sv = work + fa.w_s;
   int* ord = reinterpret_cast<int*>(work + fa.w_ord);
-  __shared__ int mdim[2][32][3];   // per column: (left, down, right) of the MPS tensors
+  __shared__ int mdim[2][kMaxGridX][3];   // per column: (left, down, right) of the MPS tensors
   __shared__ int fd[4];
   __shared__ int meta[8];
   __shared__ R slam[4 * kMaxChi];
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
           int k = 0;
           const R s0 = sv[ord[0]];
           if (s0 > R(0)) {
-            R srt[2 * 256 / 2];
+            R* srt = sv + m;   // the second half of the singular-value region
             const int nsv = m < n ? m : n;
             for (int i = 0; i < nsv; ++i) srt[i] = sv[ord[i]];
             k = team_keep_count<R>(srt, nsv, fa.chi_mps, fa.svd_cutoff, fa.multiplet_rtol);
@@ -334,25 +334,32 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
     cur ^= 1;
     tm.sync();
   }
-  if (tm.tid == 0) {
-    // contract the last MPS (vertical legs are trivial): v <- v A_x
-    R v[256], vn[256];
-    v[0] = R(1);
+  // contract the last MPS (vertical legs are trivial): v <- v A_x, the vectors in the two
+  // carry buffers (each holds at least chi_mps * final bond dimension values)
+  {
+    R* v = Cb[0];
+    R* vn = Cb[1];
+    if (tm.tid == 0) v[0] = R(1);
     int dv = 1;
+    tm.sync();
     for (int x = 0; x < nx; ++x) {
       const R* A = mps[cur] + (int64_t)x * fa.mps_stride;
       const int aL = mdim[cur][x][0], aR = mdim[cur][x][2];
-      for (int bb = 0; bb < aR && bb < 256; ++bb) {
+      const int na = aL < dv ? aL : dv;
+      for (int bb = tm.tid; bb < aR; bb += tm.nt) {
         R acc = R(0);
-        for (int a = 0; a < aL && a < dv; ++a) acc += v[a] * A[a * aR + bb];
+        for (int a = 0; a < na; ++a) acc += v[a] * A[a * aR + bb];
         vn[bb] = acc;
       }
-      dv = aR < 256 ? aR : 256;
-      for (int bb = 0; bb < dv; ++bb) v[bb] = vn[bb];
+      tm.sync();
+      R* t = v; v = vn; vn = t;
+      dv = aR;
     }
-    fa.Z[(int64_t)b * 2 + 0] = double(v[0]);
-    fa.Z[(int64_t)b * 2 + 1] = double(v[1]);
-    fa.logacc[(int64_t)b * fa.nslots + fa.slot] = logsum_s;
+    if (tm.tid == 0) {
+      fa.Z[(int64_t)b * 2 + 0] = double(v[0]);
+      fa.Z[(int64_t)b * 2 + 1] = double(v[1]);
+      fa.logacc[(int64_t)b * fa.nslots + fa.slot] = logsum_s;
+    }
   }
 }
 

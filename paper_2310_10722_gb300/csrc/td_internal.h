@@ -20,6 +20,8 @@ namespace td {
 constexpr int kMaxChi = 32;      // simple-update bond cap supported by the kernels
 constexpr int kMaxBonds = 4;     // grid sites have at most 4 bonds
 constexpr int kMaxPhys = 4;      // physical leg: vertical bit x class counter bit
+constexpr int kMaxGridX = 64;    // grid width (sites per row) of the final contraction
+constexpr int kMaxFinalBond = 1024;   // chi_mps x largest final bond dimension
 
 // One endpoint of a gate: the site tensor is stored as [phys][d_0]...[d_{nb-1}] (row
 // major, bonds ordered left, right, down, up) and viewed as [phys][outer][D][inner]

@@ -576,6 +576,7 @@ __device__ inline void svd_precond(const Team& tm, double* A, int lda, int m, in
   tm.sync();
   for (int w = tm.tid; w < m * n; w += tm.nt) A[(w / m) * lda + (w % m)] = F[w];
   if (ktop > 0 && ktop < n && nrm && ord) {
+    tm.sync();
     team_col_norms<double>(tm, A, lda, m, n, nrm);
     team_sort_desc<double>(tm, nrm, n, ord);
     for (int w = tm.tid; w < m * n; w += tm.nt) F[w] = A[ord[w / m] * lda + (w % m)];

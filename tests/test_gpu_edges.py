@@ -88,3 +88,22 @@ def test_all_zero_syndromes_and_empty_gradient(td):
     assert _close(out, su.su_logprob(dem, det, chi=8, chi_mps=8)) < 1e-6
     logP, g = net.grad_logprob(torch.zeros((0, dem.n_det), dtype=torch.uint8, device="cuda"))
     assert logP.shape == (0,) and np.all(g.cpu().numpy() == 0.0)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+def test_repeated_decodes_are_bitwise_equal(td, precision, threads):
+    """Every path is deterministic: two decodes of the same shots give the same bits (no
+    atomics in a floating-point sum, no reads racing writes), for every block size of the
+    final contraction.  3D point sector d = 5, p = 0.1, chi = 16, chi_mps = 8 (cuts of up to
+    128 columns: QR-reduced, FP32-preconditioned on the mixed paths)."""
+    import torch
+    dem = point_sector_3d(5, 0.1)
+    det, _ = sample_shots(dem, 96, seed=4005)
+    d = torch.from_numpy(det).cuda()
+    net = td.Network.from_dem(dem, chi=16, chi_mps=8, precision=precision)
+    net.set_schedule(threads, 2048, False)
+    a = net.coset_logprob(d).cpu().numpy()
+    b = net.coset_logprob(d).cpu().numpy()
+    net.check()
+    np.testing.assert_array_equal(a, b)

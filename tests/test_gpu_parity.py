@@ -158,3 +158,17 @@ def test_point_sector_d5_truncated(td, precision, tol):
     out, _ = _run(td, dem, det, chi=8, chi_mps=8, precision=precision)
     m, _ = _close(out, ref, tol)
     assert m < tol, m
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-6), (2, 1e-3)])
+def test_paper_bond_caps_chi24_chimps32(td, precision, tol):
+    """The bond caps of the paper's point-sector runs (chi_SU = 24, chi_MPS = 32, Sec. 5.1):
+    3D point sector d = 4 (truncating at these caps: cuts of up to 32 x 24 = 768 columns in
+    the final contraction) against the same-caps oracle."""
+    dem = point_sector_3d(4, 0.08)
+    det, _ = sample_shots(dem, 16, seed=41)
+    ref = su.su_logprob(dem, det, chi=24, chi_mps=32)
+    out, net = _run(td, dem, det, chi=24, chi_mps=32, precision=precision)
+    net.check()
+    m, _ = _close(out, ref, tol)
+    assert m < tol, m
