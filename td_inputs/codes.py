@@ -220,6 +220,117 @@ def repetition_phenomenological(n: int, rounds: int, p: float = 0.05, q: float =
                name=f"rep_n{n}_r{rounds}", meta=dict(kind="repetition", n=n, rounds=rounds))
 
 
+@dataclass
+class GenProblem:
+    """A CSS sector in the generator picture (Sec. 3.2): the coset of an error r is
+    r + span of the stabilizer generators, each a vertex flipping the qubits of its edges.
+
+    Qubit j is an edge of the generator graph joining one or two generators
+    (``edges[j]``, indices into the generators) and flips with probability ``p[j]``.
+    ``gen_xyt`` holds the (x, y, t) of every generator (the layered form of Sec. 4: t the
+    layer, (x, y) the site).  ``xbar`` lists the qubits of a logical operator of the flipped
+    type (the class shift: the other coset is r + xbar + span) and ``zbar`` those of the
+    conjugate logical (the class of an error is its parity on zbar).  ``face_dem`` is the same
+    problem in the detector picture (Sec. 2.4): its detectors are the checks that detect the
+    errors, its observable is zbar -- used to sample syndromes and by the exact oracles.
+    """
+    n_gen: int
+    edges: list                # list[tuple[int, ...]] generators of each qubit (1 or 2)
+    p: np.ndarray              # float64 [n_qubits]
+    gen_xyt: np.ndarray        # int32 [n_gen, 3]
+    xbar: list
+    zbar: list
+    face_dem: "DEM"
+    name: str = ""
+
+    @property
+    def n_qubits(self) -> int:
+        return len(self.edges)
+
+
+def loop_sector_3d(d: int, p: float = 0.1) -> GenProblem:
+    """Loop sector of the 3D surface code with open boundaries (Sec. 5.2): bit flips on the
+    qubits of point_sector_3d(d), detected by the plaquettes (loop-like syndromes), decoded
+    in the generator picture of the vertex stabilizers -- the point sector's lattice with the
+    roles of the + and = nodes swapped.
+
+    Generators: the d x d x (d-1) vertices (x, y, t), index t*d*d + y*d + x; qubits in the
+    order of point_sector_3d (x edges, y edges, z edges, dangling z edges at the two rough
+    boundaries).  Plaquettes: every elementary square of the lattice, those crossing a
+    rough boundary truncated to their three edges.  The logical membrane xbar is the d*d
+    dangling edges below layer 0, the conjugate string zbar the z column at (0, 0)."""
+    pt = point_sector_3d(d, p)
+    edges = [tuple(ds) for ds in pt.mech_dets]
+    nt = d - 1
+    # qubit index of every edge, by kind
+    idx = {}
+    for j, ds in enumerate(edges):
+        if len(ds) == 1:
+            v = ds[0]
+            t = v // (d * d)
+            key = ("dn", v) if (t == 0 and ("dn", v) not in idx) else ("up", v)
+            if t == 0 and t == nt - 1 and ("dn", v) in idx:
+                key = ("up", v)
+            idx[key] = j
+        else:
+            a, b = sorted(ds)
+            idx[("e", a, b)] = j
+
+    def vid(x, y, t):
+        return t * d * d + y * d + x
+
+    def edge(a, b):
+        return idx[("e", min(a, b), max(a, b))]
+
+    def zedge(x, y, t):
+        """z edge from layer t to t+1 at (x, y); t = -1 / nt - 1: the dangling edges."""
+        if t == -1:
+            return idx[("dn", vid(x, y, 0))]
+        if t == nt - 1:
+            return idx[("up", vid(x, y, nt - 1))]
+        return edge(vid(x, y, t), vid(x, y, t + 1))
+
+    faces = []
+    for t in range(nt):
+        for y in range(d - 1):
+            for x in range(d - 1):
+                faces.append((edge(vid(x, y, t), vid(x + 1, y, t)), edge(vid(x, y + 1, t), vid(x + 1, y + 1, t)),
+                              edge(vid(x, y, t), vid(x, y + 1, t)), edge(vid(x + 1, y, t), vid(x + 1, y + 1, t))))
+    for t in range(-1, nt):          # squares between layers t and t+1 (t = -1, nt-1: the rough boundaries)
+        for y in range(d):
+            for x in range(d - 1):
+                f = [zedge(x, y, t), zedge(x + 1, y, t)]
+                if t >= 0:
+                    f.append(edge(vid(x, y, t), vid(x + 1, y, t)))
+                if t + 1 <= nt - 1:
+                    f.append(edge(vid(x, y, t + 1), vid(x + 1, y, t + 1)))
+                faces.append(tuple(f))
+        for y in range(d - 1):
+            for x in range(d):
+                f = [zedge(x, y, t), zedge(x, y + 1, t)]
+                if t >= 0:
+                    f.append(edge(vid(x, y, t), vid(x, y + 1, t)))
+                if t + 1 <= nt - 1:
+                    f.append(edge(vid(x, y, t + 1), vid(x, y + 1, t + 1)))
+                faces.append(tuple(f))
+    n = len(edges)
+    mech_dets = [[] for _ in range(n)]
+    for fi, f in enumerate(faces):
+        for q in f:
+            mech_dets[q].append(fi)
+    xbar = [idx[("dn", vid(x, y, 0))] for y in range(d) for x in range(d)]
+    zbar = [zedge(0, 0, t) for t in range(-1, nt)]
+    mech_obs = [(0,) if j in set(zbar) else () for j in range(n)]
+    # face coordinates are not used by any sweep of this problem (the detector picture of the
+    # loop sector is not graph-like); each face gets a distinct dummy coordinate
+    fxyt = np.array([(fi, 0, 0) for fi in range(len(faces))], dtype=np.int32)
+    face_dem = DEM(len(faces), 1, [tuple(m) for m in mech_dets], mech_obs, np.full(n, float(p)), fxyt,
+                   name=f"loop3d_faces_d{d}", meta=dict(kind="loop3d_faces", d=d))
+    gen_xyt = np.array([(x, y, t) for t in range(nt) for y in range(d) for x in range(d)], dtype=np.int32)
+    return GenProblem(d * d * nt, edges, np.full(n, float(p)), gen_xyt, xbar, zbar, face_dem,
+                      name=f"loop3d_d{d}")
+
+
 def log_uniform_rates(dem: DEM, seed: int, lo: float = 1e-3, hi: float = 1e-2) -> DEM:
     """Replace every rate by exp(U(ln lo, ln hi)) drawn from the counter-based stream."""
     from .sampler import uniform53
