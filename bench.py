@@ -297,6 +297,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads (reported beside the line)")
     ap.add_argument("--chi16-shots", type=int, default=256, help="shots of the chi = 16 line")
     ap.add_argument("--uneven-per-size", type=int, default=152, help="shots per code size of the uneven batch")
+    ap.add_argument("--loop-shots", type=int, default=1024, help="shots of the loop-sector line")
     args = ap.parse_args()
     SHOTS = args.shots
     rank = int(os.environ.get("RANK", "0"))
@@ -480,6 +481,29 @@ def main():
             "replay_matches_eager": all(torch.equal(a, b) for a, b in zip(ref_u, outs_u))}
         for n_u in nets_u:
             n_u.close()
+
+    # loop sector of the 3D surface code (Sec. 5.2) in the generator picture (Sec. 3.2):
+    # d = 5 at p = 0.2 (near the loop threshold), chi = 8, chi_mps = 16; every shot is two
+    # sweeps (both cosets)
+    if not args.no_extra and rank == 0:
+        from td_inputs import loop_sector_3d
+        gp = loop_sector_3d(5, 0.2)
+        n_l = args.loop_shots
+        sl, _ = sample_shots(gp.face_dem, n_l, seed=6000)
+        dl = torch.from_numpy(sl).cuda()
+        res_l = {}
+        for name, pv in (("fp64", 0), (args.precision, prec)):
+            nl = td.GenNetwork.from_problem(gp, chi=8, chi_mps=16, precision=pv, mem_budget=64 << 30)
+            nl.coset_logprob(dl[:8])
+            torch.cuda.synchronize()
+            lp_l, ml = timed_decode(nl, dl, stream)
+            nl.check()
+            res_l[name] = (lp_l, _f(n_l / (ml / 1000.0)))
+            nl.close()
+        stl = coset_stats(res_l[args.precision][0], res_l["fp64"][0])
+        extra["loop_d5_p0.2_chi8_mps16"] = {"shots": n_l, "fp64": res_l["fp64"][1], args.precision: res_l[args.precision][1],
+                                            "max_dlogp_coset": stl["max_dlogp_coset"],
+                                            "max_dlogp_decision_coset": stl["max_dlogp_decision_coset"]}
 
     # gradient of the mean log P with respect to every mechanism rate: rotated d=7, 7 noisy
     # rounds + 1 perfect, per-mechanism rates log-uniform in [1e-3, 1e-2], 1024 shots per

@@ -114,6 +114,7 @@ typedef struct {
   int32_t wave;              /* shots per wave */
   int32_t chi, chi_mps, precision;
   int32_t offset_all;        /* 1 if the observable was replaced by l + sum of rows of H */
+  int32_t generator;         /* 1 for a generator network (td_build_gen_network) */
   size_t workspace_bytes;    /* device bytes held by the network */
   int64_t launches_per_wave; /* kernel launches enqueued per wave */
 } td_network_info;
@@ -214,6 +215,71 @@ td_status td_grad_logprob(td_network* net, const uint8_t* det_dev, int64_t B, co
  * `stream` and the call returns without waiting for them. */
 td_status td_grad_logprob_forced(td_network* net, const uint8_t* det_dev, int64_t B, const double* p_dev,
                                  double* logP_dev, double* grad_dev, void* stream);
+
+/* ---- Generator networks (Sec. 3.2; the loop sector of Sec. 5.2) ------------------------
+ *
+ * A CSS sector decoded in the generator picture: qubit j flips independently with rate p_j,
+ * n_checks checks (the rows of H) observe the flips, and n_gen stabilizer generators of the
+ * other type span the errors equivalent to none -- generator v flips the qubits that name it.
+ * For a syndrome m, the class-L coset probability is
+ *     p_{m,L} = sum over x with H x = m and (x . zbar) = L of prod_j p_j^{x_j} (1-p_j)^{1-x_j}
+ * (Sec. 2.4 with the observable zbar), computed as the coset sum of Sec. 3.2: with r a
+ * representative of m, p(coset of r) = sum over s in {0,1}^{n_gen} of
+ * prod_j w_j(r_j + sum_{v flipping j} s_v), w_j = (1 - p_j, p_j), divided by 2^(n_gen - rank)
+ * when the generators are dependent; the classes are the cosets of r and r + xbar.  The
+ * network has one weight per qubit between the generators it touches and is contracted as
+ * in Sec. 4: a PEPS over the generators of one layer (physical leg = the generator's bit),
+ * swept along t; in-layer qubits are the diagonal two-site gates diag(w(r + s_a + s_b)),
+ * each followed by the simple-update truncation to chi; the final 2D network by the boundary
+ * MPS (chi_mps).  Nonnegative throughout: the class is carried by the representative.
+ *
+ * Representative: r is the error supported on the greedy column basis of H (columns in qubit
+ * order, a column kept when it is independent of those kept before it) with H r = m; it is
+ * unique and computed on the device from a GF(2) elimination done at build time.  A truncated
+ * contraction depends on the representative; this rule fixes it.
+ *
+ * Geometry: gen_xyt places every generator at (x, y, t); every occupied (x, y) holds one
+ * generator in every layer t = 0 .. T-1.  A qubit names one or two generators: two in one
+ * layer at grid neighbours (an in-layer edge), two at one (x, y) in consecutive layers (a
+ * vertical edge), or one (a dangling edge).  Every generator of layer t > 0 has exactly one
+ * vertical edge from layer t-1; every generator of layer 0 one dangling edge below and every
+ * generator of layer T-1 one dangling edge above (in qubit order, a layer-0 generator's first
+ * dangling edge is the one below).  Other geometries are TD_ERR_UNSUPPORTED. */
+typedef struct {
+  int32_t n_gen;               /* stabilizer generators of the other type (vertices) */
+  int32_t n_qubits;            /* qubits (edges) */
+  int32_t n_checks;            /* checks (rows of H; the syndrome's length) */
+  const int32_t* qubit_gens;   /* [n_qubits][2] generators flipping each qubit; [j][1] = -1 for a
+                                  dangling edge */
+  const double* p;             /* [n_qubits] flip rates, each in [0, 1] */
+  const int32_t* gen_xyt;      /* [n_gen][3] (x, y, t) of every generator */
+  const int32_t* check_indptr; /* [n_checks + 1] CSR of H by rows */
+  const int32_t* check_indices;/* qubit indices of each check */
+  int32_t n_xbar;              /* xbar: a logical of the flipped type (H xbar = 0, not a sum of */
+  const int32_t* xbar;         /*   generators): qubit indices */
+  int32_t n_zbar;              /* zbar: its conjugate logical (even overlap with every generator, */
+  const int32_t* zbar;         /*   odd with xbar): qubit indices; the class of x is x . zbar */
+} td_gen;
+
+/* Build the generator network of `gen` (host arrays, copied) and allocate its workspace.
+ * The decoding calls of a generator network are td_gen_coset_logprob and td_gen_decode;
+ * the detector-network calls (td_coset_logprob and its variants, the gradients, the tuner and
+ * td_debug_sweep) return TD_ERR_INVALID on it.  Errors: TD_ERR_INVALID (shapes, ranges, p
+ * outside [0, 1], a generator that anticommutes with a check -- H g_v != 0 --, xbar with a
+ * syndrome, zbar that anticommutes with a generator or commutes with xbar),
+ * TD_ERR_UNSUPPORTED (the geometry rules above, chi > 32), TD_ERR_OOM, TD_ERR_CUDA. */
+td_status td_build_gen_network(const td_gen* gen, const td_options* opt, td_network** out);
+
+/* Coset log-probabilities of a generator network.  syn_dev: device uint8 [B][n_checks], each
+ * 0 or 1.  logp_dev: device double [B][2]; logp_dev[b][L] = log p_{m_b, L}; both -inf when
+ * m_b is not a syndrome (no error has it).  Each shot is two sweeps (r and r + xbar), run as
+ * two rows of the network's waves.  B >= 0.  Asynchronous on `stream`. */
+td_status td_gen_coset_logprob(td_network* net, const uint8_t* syn_dev, int64_t B, double* logp_dev, void* stream);
+
+/* Decisions argmax_L p_{m,L} (ties -> 0) and margins of a generator network (as td_decode).
+ * decision_dev: device int32 [B]; margin_dev: device double [B] or NULL. */
+td_status td_gen_decode(td_network* net, const uint8_t* syn_dev, int64_t B, int32_t* decision_dev,
+                        double* margin_dev, void* stream);
 
 /* Launch schedule of the network (a property of this library; the paper has none): the
  * block size of the final contraction's kernel (256, 512 or 1024 threads; the Jacobi lane

@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import TD_FP32, TD_FP64, TD_TC, TDError, check
 
-__all__ = ["Network", "TDError", "TD_FP64", "TD_FP32", "TD_TC", "load_library"]
+__all__ = ["Network", "GenNetwork", "TDError", "TD_FP64", "TD_FP32", "TD_TC", "load_library"]
 
 
 def load_library():
@@ -204,6 +204,74 @@ class Network:
             self.close()
         except Exception:
             pass
+
+
+class GenNetwork(Network):
+    """A generator network (td_build_gen_network, Sec. 3.2): a CSS sector decoded in the
+    generator picture, e.g. the loop sector of the 3D surface code (Sec. 5.2).
+
+    qubit_gens [n_qubits][2]: the generators flipping each qubit (second -1 for a dangling
+    edge); p the flip rates; gen_xyt [n_gen][3]; the checks H in CSR by rows; xbar, zbar
+    the qubits of the flipped-type logical and of its conjugate (the class of an error).
+    """
+
+    def __init__(self, qubit_gens, p, gen_xyt, check_indptr, check_indices, xbar, zbar, *, chi=8, chi_mps=16,
+                 precision=TD_FP64, svd_cutoff=1e-12, multiplet_rtol=1e-8, gram_cutoff=None, mem_budget=0,
+                 max_wave=0):
+        lib = _lib.load()
+        self._lib = lib
+        qg = _i32(qubit_gens).reshape(-1)
+        self._keep = [qg, np.ascontiguousarray(np.asarray(p, dtype=np.float64)), _i32(gen_xyt).reshape(-1),
+                      _i32(check_indptr), _i32(check_indices), _i32(xbar), _i32(zbar)]
+        qg, pp, xyt, cip, cix, xb, zb = self._keep
+        P = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+        g = _lib.td_gen(len(xyt) // 3, len(qg) // 2, len(cip) - 1, P(qg, C.c_int32), P(pp, C.c_double),
+                        P(xyt, C.c_int32), P(cip, C.c_int32), P(cix, C.c_int32), len(xb), P(xb, C.c_int32),
+                        len(zb), P(zb, C.c_int32))
+        opt = _lib.td_options()
+        lib.td_default_options(C.byref(opt))
+        opt.chi, opt.chi_mps, opt.precision = chi, chi_mps, precision
+        opt.svd_cutoff, opt.multiplet_rtol = svd_cutoff, multiplet_rtol
+        if gram_cutoff is not None:
+            opt.gram_cutoff = gram_cutoff
+        if mem_budget:
+            opt.mem_budget = mem_budget
+        opt.max_wave = max_wave
+        h = C.c_void_p()
+        check(lib.td_build_gen_network(C.byref(g), C.byref(opt), C.byref(h)))
+        self._h = h
+        self.n_checks = len(cip) - 1
+        self.n_qubits = len(qg) // 2
+        self.n_det, self.n_mech, self.n_obs, self.n_class = self.n_checks, self.n_qubits, 1, 2
+
+    @classmethod
+    def from_problem(cls, gp, **kw):
+        """Build from a td_inputs.GenProblem (edges, p, gen_xyt, xbar, zbar, face_dem)."""
+        qg = np.array([list(e) + [-1] * (2 - len(e)) for e in gp.edges], dtype=np.int32)
+        hip, hix = gp.face_dem.H_csr()
+        return cls(qg, gp.p, gp.gen_xyt, hip, hix, list(gp.xbar), list(gp.zbar), **kw)
+
+    def coset_logprob(self, syn, out=None, stream=None):
+        """log p_{m,L} for every shot: CUDA float64 [B, 2] (syn: CUDA uint8 [B, n_checks])."""
+        import torch
+        self._check_det(syn)
+        B = syn.shape[0]
+        if out is None:
+            out = torch.empty((B, 2), dtype=torch.float64, device=syn.device)
+        check(self._lib.td_gen_coset_logprob(self._h, C.c_void_p(syn.data_ptr()), B, C.c_void_p(out.data_ptr()),
+                                             self._stream(stream)))
+        return out
+
+    def decode(self, syn, stream=None):
+        """(decision int32 [B], margin float64 [B]) on the device."""
+        import torch
+        self._check_det(syn)
+        B = syn.shape[0]
+        dec = torch.empty(B, dtype=torch.int32, device=syn.device)
+        mar = torch.empty(B, dtype=torch.float64, device=syn.device)
+        check(self._lib.td_gen_decode(self._h, C.c_void_p(syn.data_ptr()), B, C.c_void_p(dec.data_ptr()),
+                                      C.c_void_p(mar.data_ptr()), self._stream(stream)))
+        return dec, mar
 
 
 def fma_peak_tflops(fp64: bool = True, iters: int = 1 << 16, stream=None) -> float:

@@ -17,7 +17,8 @@ EXPORTS = ["td_default_options", "td_build_network", "td_coset_logprob", "td_dec
            "td_coset_logprob_host", "td_grad_logprob", "td_grad_logprob_forced", "td_network_set_schedule",
            "td_network_tune", "td_network_get_info", "td_debug_sweep",
            "td_network_profile", "td_network_get_work", "td_coset_logprob_static", "td_free_network",
-           "td_network_check", "td_measure_fma_peak", "td_last_error"]
+           "td_network_check", "td_measure_fma_peak", "td_build_gen_network", "td_gen_coset_logprob",
+           "td_gen_decode", "td_last_error"]
 
 
 class td_dem(C.Structure):
@@ -25,6 +26,14 @@ class td_dem(C.Structure):
                 ("H_indptr", C.POINTER(C.c_int32)), ("H_indices", C.POINTER(C.c_int32)),
                 ("L_indptr", C.POINTER(C.c_int32)), ("L_indices", C.POINTER(C.c_int32)),
                 ("p", C.POINTER(C.c_double))]
+
+
+class td_gen(C.Structure):
+    _fields_ = [("n_gen", C.c_int32), ("n_qubits", C.c_int32), ("n_checks", C.c_int32),
+                ("qubit_gens", C.POINTER(C.c_int32)), ("p", C.POINTER(C.c_double)),
+                ("gen_xyt", C.POINTER(C.c_int32)), ("check_indptr", C.POINTER(C.c_int32)),
+                ("check_indices", C.POINTER(C.c_int32)), ("n_xbar", C.c_int32), ("xbar", C.POINTER(C.c_int32)),
+                ("n_zbar", C.c_int32), ("zbar", C.POINTER(C.c_int32))]
 
 
 class td_layout(C.Structure):
@@ -41,7 +50,8 @@ class td_network_info(C.Structure):
     _fields_ = [("n_sites", C.c_int32), ("n_layers", C.c_int32), ("n_bonds", C.c_int32),
                 ("n_gates", C.c_int32), ("n_counter_sites", C.c_int32), ("nx", C.c_int32),
                 ("ny", C.c_int32), ("wave", C.c_int32), ("chi", C.c_int32), ("chi_mps", C.c_int32),
-                ("precision", C.c_int32), ("offset_all", C.c_int32), ("workspace_bytes", C.c_size_t),
+                ("precision", C.c_int32), ("offset_all", C.c_int32), ("generator", C.c_int32),
+                ("workspace_bytes", C.c_size_t),
                 ("launches_per_wave", C.c_int64)]
 
 
@@ -94,6 +104,12 @@ def load(path: str | None = None):
     lib.td_network_check.restype = C.c_int
     lib.td_measure_fma_peak.argtypes = [C.c_int32, C.c_int32, vp, vp]
     lib.td_measure_fma_peak.restype = C.c_int
+    lib.td_build_gen_network.argtypes = [C.POINTER(td_gen), C.POINTER(td_options), C.POINTER(vp)]
+    lib.td_build_gen_network.restype = C.c_int
+    lib.td_gen_coset_logprob.argtypes = [vp, vp, C.c_int64, vp, vp]
+    lib.td_gen_coset_logprob.restype = C.c_int
+    lib.td_gen_decode.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+    lib.td_gen_decode.restype = C.c_int
     lib.td_free_network.argtypes = [vp]
     lib.td_free_network.restype = None
     lib.td_last_error.argtypes = []

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["api.cu", "sweep.cu", "absorb.cu", "core.cu", "final.cu", "grad.cu", "adjoint.cu", "probe.cu", "plan.cpp"]
+SOURCES = ["api.cu", "sweep.cu", "absorb.cu", "core.cu", "final.cu", "grad.cu", "adjoint.cu", "probe.cu", "gen.cu", "plan.cpp"]
 
 
 def _nvcc():

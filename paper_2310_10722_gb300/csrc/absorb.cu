@@ -5,7 +5,10 @@
 // with Y = M[sigma_lo] + M[sigma_hi] and Z = M[sigma_lo] - M[sigma_hi] for each physical
 // pair sigma_hi = sigma_lo ^ mask, the Gram of the doubled side matrix is block diagonal,
 // G+ = sum_rows Y^T Y and G- = sum_rows Z^T Z (rows weighted by the other bonds' lambda), and
-// the update is Gamma_new[lo] = Y T+ + Z T-, Gamma_new[hi] = Y T+ - Z T-.
+// the update is Gamma_new[lo] = Y T+ + Z T-, Gamma_new[hi] = Y T+ - Z T-.  The diagonal gate
+// diag(w(r + s_a + s_b)) of the generator picture (Sec. 3.2; GateDesc.diag) doubles its bond
+// with kappa = the physical bit: Y = M[sigma_lo], Z = M[sigma_hi], and the update is
+// Gamma_new[lo] = Y T0, Gamma_new[hi] = Z T1.
 //
 // A side tensor is [phys][outer][D][inner]; a row is (pair, outer index o, inner index i)
 // and holds D values at stride `inner`.  Each row is handled by LPR lanes; lane `sub` of a
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(256) k_gram(SweepArgs a, const GateDesc* __res
   const Job jb = decode_job(job, nchunk, a.B);
   const GateDesc& gd = gates[jb.gi];
   const SideDesc sd = gd.side[jb.side];
+  const bool dg = gd.diag != 0;   // diagonal gate: the blocks are lo and hi themselves
   const int D = gd.D;
   const double* lamb = a.lam + (int64_t)jb.b * a.nbonds * chi;
   for (int w = lane; w < kMaxBonds * chi; w += 32) {
@@ -174,8 +178,8 @@ __global__ void __launch_bounds__(256) k_gram(SweepArgs a, const GateDesc* __res
           lo = double(plo[(int64_t)q * sd.inner]);
           hi = double(phi[(int64_t)q * sd.inner]);
         }
-        yo[k] = (lo + hi) * w;
-        zo[k] = (lo - hi) * w;
+        yo[k] = (dg ? lo : lo + hi) * w;
+        zo[k] = (dg ? hi : lo - hi) * w;
       }
     }
     double y[DMAX], z[DMAX];
@@ -244,6 +248,7 @@ __global__ void __launch_bounds__(256) k_gram_sym8(SweepArgs a, const GateDesc* 
   const Job jb = decode_job(job, nchunk, a.B);
   const GateDesc& gd = gates[jb.gi];
   const SideDesc sd = gd.side[jb.side];
+  const bool dg = gd.diag != 0;   // diagonal gate: the blocks are lo and hi themselves
   const int D = gd.D;
   const double* lamb = a.lam + (int64_t)jb.b * a.nbonds * chi;
   for (int w = lane; w < kMaxBonds * chi; w += 32) {
@@ -289,8 +294,8 @@ __global__ void __launch_bounds__(256) k_gram_sym8(SweepArgs a, const GateDesc* 
           lo = double(plo[(int64_t)q * sd.inner]);
           hi = double(phi[(int64_t)q * sd.inner]);
         }
-        yo[k] = (lo + hi) * w;
-        zo[k] = (lo - hi) * w;
+        yo[k] = (dg ? lo : lo + hi) * w;
+        zo[k] = (dg ? hi : lo - hi) * w;
       }
     }
     double y[8], z[8];
@@ -356,6 +361,7 @@ __global__ void __launch_bounds__(256) k_gram_sym16(SweepArgs a, const GateDesc*
   const Job jb = decode_job(job, nchunk, a.B);
   const GateDesc& gd = gates[jb.gi];
   const SideDesc sd = gd.side[jb.side];
+  const bool dg = gd.diag != 0;   // diagonal gate: the blocks are lo and hi themselves
   const int D = gd.D;
   const double* lamb = a.lam + (int64_t)jb.b * a.nbonds * chi;
   for (int w = lane; w < kMaxBonds * chi; w += 32) {
@@ -401,8 +407,8 @@ __global__ void __launch_bounds__(256) k_gram_sym16(SweepArgs a, const GateDesc*
           lo = double(plo[(int64_t)q * sd.inner]);
           hi = double(phi[(int64_t)q * sd.inner]);
         }
-        yo[k] = (lo + hi) * w;
-        zo[k] = (lo - hi) * w;
+        yo[k] = (dg ? lo : lo + hi) * w;
+        zo[k] = (dg ? hi : lo - hi) * w;
       }
     }
     double y[16], z[16];
@@ -459,6 +465,7 @@ __global__ void __launch_bounds__(256) k_update(SweepArgs a, const GateDesc* __r
   const Job jb = decode_job(job, nchunk, a.B);
   const GateDesc& gd = gates[jb.gi];
   const SideDesc sd = gd.side[jb.side];
+  const bool dg = gd.diag != 0;   // diagonal gate: the blocks are lo and hi themselves
   const int D = gd.D, Dn = gd.Dn;
   const double* tsrc = tbuf + jb.gb * 4 * chi * chi + (int64_t)jb.side * 2 * chi * chi;
   for (int w = lane; w < DMAX * DMAX; w += 32) {
@@ -500,8 +507,8 @@ __global__ void __launch_bounds__(256) k_update(SweepArgs a, const GateDesc* __r
           lo = double(plo[(int64_t)q * sd.inner]);
           hi = double(phi[(int64_t)q * sd.inner]);
         }
-        yo[k] = lo + hi;
-        zo[k] = lo - hi;
+        yo[k] = dg ? lo : lo + hi;
+        zo[k] = dg ? hi : lo - hi;
       }
     }
     double y[DMAX], z[DMAX];
@@ -522,8 +529,8 @@ __global__ void __launch_bounds__(256) k_update(SweepArgs a, const GateDesc* __r
         u2 += z[q] * Tm[q * DMAX + j];
       }
       if (live && j < Dn) {
-        qlo[(int64_t)j * sd.inner] = T(u1 + u2);
-        qhi[(int64_t)j * sd.inner] = T(u1 - u2);
+        qlo[(int64_t)j * sd.inner] = T(dg ? u1 : u1 + u2);
+        qhi[(int64_t)j * sd.inner] = T(dg ? u2 : u1 - u2);
       }
     }
   }
@@ -726,6 +733,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_tc(SweepArgs a, const Ga
     const Job jb = decode_job(job, nchunk, a.B);
     const GateDesc& gd = gates[jb.gi];
     const SideDesc sd = gd.side[jb.side];
+    const bool dg = gd.diag != 0;   // diagonal gate: the blocks are lo and hi themselves
     const int D = gd.D;
     const double* lamb = a.lam + (int64_t)jb.b * a.nbonds * chi;
     for (int w = tid; w < kMaxBonds * chi; w += kTcThreads) {
@@ -819,13 +827,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_gram_tc(SweepArgs a, const Ga
               float y1, y2;
               const double w0 = wt[k0], w1 = wt[k0 + 1];
               const float w0a = (float)w0, w1a = (float)w1;
-              tc_pair(lo8[2 * v], pt ? -hi8[2 * v] : hi8[2 * v], w0a, (float)(w0 - (double)w0a), y1, y2);
+              // X x X gate: (lo + hi) w, (lo - hi) w; diagonal gate: lo w, hi w
+              const float a0 = dg ? (pt ? 0.f : lo8[2 * v]) : lo8[2 * v];
+              const float b0 = dg ? (pt ? hi8[2 * v] : 0.f) : (pt ? -hi8[2 * v] : hi8[2 * v]);
+              const float a1 = dg ? (pt ? 0.f : lo8[2 * v + 1]) : lo8[2 * v + 1];
+              const float b1 = dg ? (pt ? hi8[2 * v + 1] : 0.f) : (pt ? -hi8[2 * v + 1] : hi8[2 * v + 1]);
+              tc_pair(a0, b0, w0a, (float)(w0 - (double)w0a), y1, y2);
               tc_slices32(y1 * sc, y2 * sc, t0);
-              tc_pair(lo8[2 * v + 1], pt ? -hi8[2 * v + 1] : hi8[2 * v + 1], w1a, (float)(w1 - (double)w1a), y1, y2);
+              tc_pair(a1, b1, w1a, (float)(w1 - (double)w1a), y1, y2);
               tc_slices32(y1 * sc, y2 * sc, t1);
             } else {
-              tc_slices64((pt ? lo8[2 * v] - hi8[2 * v] : lo8[2 * v] + hi8[2 * v]) * wt[k0], E, t0);
-              tc_slices64((pt ? lo8[2 * v + 1] - hi8[2 * v + 1] : lo8[2 * v + 1] + hi8[2 * v + 1]) * wt[k0 + 1], E, t1);
+              // X x X gate: (lo + hi) w, (lo - hi) w; diagonal gate: lo w, hi w
+              const double y0 = dg ? (pt ? hi8[2 * v] : lo8[2 * v]) : (pt ? lo8[2 * v] - hi8[2 * v] : lo8[2 * v] + hi8[2 * v]);
+              const double y1v = dg ? (pt ? hi8[2 * v + 1] : lo8[2 * v + 1])
+                                    : (pt ? lo8[2 * v + 1] - hi8[2 * v + 1] : lo8[2 * v + 1] + hi8[2 * v + 1]);
+              tc_slices64(y0 * wt[k0], E, t0);
+              tc_slices64(y1v * wt[k0 + 1], E, t1);
             }
 #pragma unroll
             for (int i = 0; i < kTcSlices; ++i) {

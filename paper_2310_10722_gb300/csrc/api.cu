@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "gen.cuh"
 #include "sweep.cuh"
 #include "td_internal.h"
 #include "team.cuh"
@@ -89,6 +90,14 @@ struct td_network {
          *d_gfscr = nullptr, *d_Kbar = nullptr, *d_pbar = nullptr, *d_Rbar = nullptr, *d_glogp = nullptr;
   td::AdjArgs adj{};
   td::FinalArgs gfin{};
+  // generator network: elimination transform, pivot columns, xbar, and per-chunk rows
+  unsigned long long* d_gen_trans = nullptr;
+  int32_t* d_gen_col = nullptr;
+  uint8_t* d_gen_xbar = nullptr;
+  uint8_t* d_gen_rows = nullptr;     // [2 gen_chunk][n_qubits]
+  int32_t* d_gen_cls = nullptr;      // [gen_chunk]
+  double* d_gen_lp = nullptr;        // [2 gen_chunk][2]
+  int64_t gen_chunk = 0;             // shots per chunk (two sweep rows each)
   td_dem dem_view(const double* p) const {
     td_dem d{};
     d.n_det = plan.n_det; d.n_mech = plan.n_mech; d.n_obs = n_obs;
@@ -239,6 +248,8 @@ void td_default_options(td_options* opt) {
 
 const char* td_last_error(void) { return g_err.c_str(); }
 
+static td_status finish_build(td_network* net, const td_options& o, td_network** out);
+
 td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_options* opt, td_network** out) {
   g_err.clear();
   if (!dem || !layout || !out) return fail(TD_ERR_INVALID, "null argument");
@@ -250,8 +261,6 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   std::string err;
   td_status st = td::build_plan(*dem, *layout, o, net->plan, err);
   if (st != TD_OK) { delete net; return fail(st, err); }
-  td::Plan& P = net->plan;
-  if (P.nx > td::kMaxGridX) { delete net; return fail(TD_ERR_UNSUPPORTED, "grid wider than 64 sites"); }
   net->H_indptr.assign(dem->H_indptr, dem->H_indptr + dem->n_det + 1);
   net->H_indices.assign(dem->H_indices, dem->H_indices + dem->H_indptr[dem->n_det]);
   net->L_indptr.assign(dem->L_indptr, dem->L_indptr + dem->n_obs + 1);
@@ -259,6 +268,30 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
   net->det_xyt.assign(layout->det_xyt, layout->det_xyt + 3 * (size_t)dem->n_det);
   net->rates.assign(dem->p, dem->p + dem->n_mech);
   net->n_obs = dem->n_obs;
+  return finish_build(net, o, out);
+}
+
+td_status td_build_gen_network(const td_gen* gen, const td_options* opt, td_network** out) {
+  g_err.clear();
+  if (!gen || !out) return fail(TD_ERR_INVALID, "null argument");
+  *out = nullptr;
+  td_options o;
+  if (opt) o = *opt; else td_default_options(&o);
+  td_network* net = new (std::nothrow) td_network();
+  if (!net) return fail(TD_ERR_OOM, "host allocation failed");
+  std::string err;
+  td_status st = td::build_gen_plan(*gen, o, net->plan, err);
+  if (st != TD_OK) { delete net; return fail(st, err); }
+  if (net->plan.check_words > 3000) { delete net; return fail(TD_ERR_UNSUPPORTED, "more than 192000 checks"); }
+  net->n_obs = 1;
+  net->rates.assign(gen->p, gen->p + gen->n_qubits);
+  return finish_build(net, o, out);
+}
+
+// Device workspace of a planned network (both kinds); deletes net on failure.
+static td_status finish_build(td_network* net, const td_options& o, td_network** out) {
+  td::Plan& P = net->plan;
+  if (P.nx > td::kMaxGridX) { delete net; return fail(TD_ERR_UNSUPPORTED, "grid wider than 64 sites"); }
   net->opt = o;
   const int chi = P.chi, cm = P.chi_mps, Dm = P.max_final_D;
   if ((int64_t)cm * Dm > td::kMaxFinalBond) {
@@ -318,6 +351,15 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
             net->alloc(net->d_det_stage, (size_t)wave * P.n_det) &&
             net->alloc(net->d_logp_stage, (size_t)wave * 2 * 8) &&
             net->alloc(net->d_status, sizeof(int));
+  if (ok && P.gen) {
+    net->gen_chunk = std::max<int64_t>(1, wave / 2);
+    ok = net->alloc(net->d_gen_trans, sizeof(unsigned long long) * P.gen_rows.size()) &&
+         net->alloc(net->d_gen_col, sizeof(int32_t) * std::max<size_t>(P.gen_col.size(), 1)) &&
+         net->alloc(net->d_gen_xbar, P.gen_xbar.size()) &&
+         net->alloc(net->d_gen_rows, (size_t)2 * net->gen_chunk * P.n_qubits) &&
+         net->alloc(net->d_gen_cls, sizeof(int32_t) * net->gen_chunk) &&
+         net->alloc(net->d_gen_lp, sizeof(double) * 4 * net->gen_chunk);
+  }
   if (!ok) { delete net; return fail(TD_ERR_OOM, "device allocation failed"); }
   cudaError_t e;
   if ((!P.gates.empty() && (e = cudaMemcpy(net->d_gates, P.gates.data(), sizeof(td::GateDesc) * P.gates.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
@@ -327,10 +369,17 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
     delete net;
     return cuda_fail(e, "descriptor upload");
   }
+  if (P.gen &&
+      ((e = cudaMemcpy(net->d_gen_trans, P.gen_rows.data(), sizeof(unsigned long long) * P.gen_rows.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+       (!P.gen_col.empty() && (e = cudaMemcpy(net->d_gen_col, P.gen_col.data(), sizeof(int32_t) * P.gen_col.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+       (e = cudaMemcpy(net->d_gen_xbar, P.gen_xbar.data(), P.gen_xbar.size(), cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    delete net;
+    return cuda_fail(e, "generator tables upload");
+  }
   if ((e = cudaMemset(net->d_status, 0, sizeof(int))) != cudaSuccess) { delete net; return cuda_fail(e, "status init"); }
   // pageable uploads may still be in flight when cudaMemcpy returns
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) { delete net; return cuda_fail(e, "descriptor upload"); }
-  int64_t launches = 1 + 2;   // init, final, finalize
+  int64_t launches = 1 + 2 + (P.gen ? 2 : 0);   // init, final, finalize (+ rows, combine)
   const int per_round = 3;   // Gram, core, update
   for (const td::LayerPlan& L : P.layers) launches += 1 + per_round * (int64_t)L.rounds.size();
   net->launches_per_wave = launches;
@@ -451,6 +500,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
 
 static td_status check_call(td_network* net, const void* det, int64_t B) {
   if (!net) return fail(TD_ERR_INVALID, "null network");
+  if (net->plan.gen) return fail(TD_ERR_INVALID, "generator network: decode with td_gen_coset_logprob / td_gen_decode");
   if (B < 0) return fail(TD_ERR_INVALID, "B must be >= 0");
   if (B > 0 && !det) return fail(TD_ERR_INVALID, "null detector buffer");
   if (B > (int64_t)1 << 31) return fail(TD_ERR_INVALID, "B too large");
@@ -472,6 +522,74 @@ td_status td_decode(td_network* net, const uint8_t* det_dev, int64_t B, int32_t*
   if (s != TD_OK) return s;
   if (B > 0 && !decision_dev) return fail(TD_ERR_INVALID, "null decision buffer");
   return run(net, det_dev, B, nullptr, decision_dev, margin_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static td_status run_gen(td_network* net, const uint8_t* syn, int64_t B, double* logp, int32_t* decision,
+                         double* margin, cudaStream_t st) {
+  td::Plan& P = net->plan;
+  for (int64_t c0 = 0; c0 < B; c0 += net->gen_chunk) {
+    const int64_t Bc = std::min<int64_t>(net->gen_chunk, B - c0);
+    td::GenRowsArgs g{};
+    g.syn = syn + c0 * P.n_checks;
+    g.B = Bc;
+    g.n_checks = P.n_checks;
+    g.words = P.check_words;
+    g.trans = net->d_gen_trans;
+    g.rank = P.gen_rank;
+    g.col = net->d_gen_col;
+    g.xbar = net->d_gen_xbar;
+    g.n_cols = P.n_qubits;
+    g.rows = net->d_gen_rows;
+    g.cls = net->d_gen_cls;
+    cudaError_t e;
+    {
+      td_network::Mark mk(net, TD_K_INIT, st);
+      e = td::launch_gen_rows(g, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "representative launch");
+    td_status s = run(net, net->d_gen_rows, 2 * Bc, net->d_gen_lp, nullptr, nullptr, st);
+    if (s != TD_OK) return s;
+    td::GenCombineArgs z{};
+    z.row_logp = net->d_gen_lp;
+    z.cls = net->d_gen_cls;
+    z.B = Bc;
+    z.log_offset = P.gen_log_offset;
+    z.logp = logp ? logp + 2 * c0 : nullptr;
+    z.decision = decision ? decision + c0 : nullptr;
+    z.margin = margin ? margin + c0 : nullptr;
+    {
+      td_network::Mark mk(net, TD_K_FINALIZE, st);
+      e = td::launch_gen_combine(z, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "class combine launch");
+  }
+  return TD_OK;
+}
+
+static td_status check_gen_call(td_network* net, const void* syn, int64_t B) {
+  if (!net) return fail(TD_ERR_INVALID, "null network");
+  if (!net->plan.gen) return fail(TD_ERR_INVALID, "detector network: decode with td_coset_logprob / td_decode");
+  if (B < 0) return fail(TD_ERR_INVALID, "B must be >= 0");
+  if (B > 0 && !syn) return fail(TD_ERR_INVALID, "null syndrome buffer");
+  if (B > (int64_t)1 << 30) return fail(TD_ERR_INVALID, "B too large");
+  return TD_OK;
+}
+
+td_status td_gen_coset_logprob(td_network* net, const uint8_t* syn_dev, int64_t B, double* logp_dev, void* stream) {
+  g_err.clear();
+  td_status s = check_gen_call(net, syn_dev, B);
+  if (s != TD_OK) return s;
+  if (B > 0 && !logp_dev) return fail(TD_ERR_INVALID, "null output buffer");
+  return run_gen(net, syn_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+td_status td_gen_decode(td_network* net, const uint8_t* syn_dev, int64_t B, int32_t* decision_dev, double* margin_dev,
+                        void* stream) {
+  g_err.clear();
+  td_status s = check_gen_call(net, syn_dev, B);
+  if (s != TD_OK) return s;
+  if (B > 0 && !decision_dev) return fail(TD_ERR_INVALID, "null decision buffer");
+  return run_gen(net, syn_dev, B, nullptr, decision_dev, margin_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
 td_status td_coset_logprob_host(td_network* net, const uint8_t* det_host, int64_t B, double* logp_host, void* stream) {
@@ -1124,6 +1242,7 @@ td_status td_network_get_info(const td_network* net, td_network_info* info) {
   info->chi_mps = P.chi_mps;
   info->precision = P.precision;
   info->offset_all = P.offset_all;
+  info->generator = P.gen;
   info->workspace_bytes = net->bytes;
   info->launches_per_wave = net->launches_per_wave;
   return TD_OK;

@@ -6,6 +6,8 @@
 // decomposition, so the two-site core of the simple update is
 //     theta = [c(ka, kb) R_{A ka} Lambda R_{B kb}^T],  c(+,+) = c(-,-) = 1/2,
 //     c(+,-) = c(-,+) = (1 - 2p)/2,
+// (for the diagonal gate diag(w(r + s_a + s_b)) of the generator picture kappa is the
+// physical bit, the blocks are the lo and hi rows themselves and c(ka, kb) = w(r + ka + kb)),
 // a (rA x rB) matrix, rA, rB <= 2D.  Its SVD theta = U S V^T is truncated to k <= chi values
 // (cutoff and multiplet rule), the bond weight becomes S/s_1 (ln s_1 to the log-scale) and
 // the update transforms T_{X kappa} = R_{X kappa}^+ [U or V]_{kappa rows, :k} / sqrt2 are
@@ -141,7 +143,15 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
   }
   const Override* ov = vshot_ovr(a.vs, a.ovr, a.wave_first, b, kOvrGate, a.gate_base + gi);
   const double p = ov ? ov->val[0] : gd.p;
-  const double cpp = 0.5, cpm = 0.5 * (1.0 - 2.0 * p);
+  // core coefficients c(ka, kb): kappa = +/- for the gate (1-p) I x I + p X x X; for the
+  // diagonal gate of the generator picture kappa is the physical bit itself and
+  // c(ka, kb) = w(r + ka + kb), w = (1-p, p), with r the shot's bit of the gate's qubit
+  double c_eq = 0.5, c_ne = 0.5 * (1.0 - 2.0 * p);
+  if (gd.diag) {
+    const int r = a.det[(int64_t)vshot_row(a.vs, a.wave_first, b) * a.n_det + gd.rcol] & 1;
+    c_eq = r ? p : 1.0 - p;
+    c_ne = r ? 1.0 - p : p;
+  }
   for (int w = tm.tid; w < rA * D; w += tm.nt) {     // R_A Lambda, in place
     const int i = w / D, q = w % D;
     const int ka = i < rAp ? 0 : 1, li = i - ka * rAp;
@@ -158,7 +168,7 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
     const double* rb = Rm + (2 + kb) * DD + lj * D;
     double s = 0.0;
     for (int q = 0; q < D; ++q) s += ra[q] * rb[q];
-    TH[j * ldt + i] = (ka == kb ? cpp : cpm) * s;
+    TH[j * ldt + i] = (ka == kb ? c_eq : c_ne) * s;
   }
   tm.sync();
   if (precond)
@@ -195,7 +205,7 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
   }
   for (int j = tm.tid; j < k; j += tm.nt) sm.aux[j] = 1.0 / sm.sv[sm.order[j]];
   tm.sync();
-  const double rs2 = 0.70710678118654752440;
+  const double rs2 = gd.diag ? 1.0 : 0.70710678118654752440;   // the kappa basis' 1/sqrt2
   // T_{A kap}[q][j] = sum_{li} R^+_{A kap}[q][li] U[kap rows li][order j] / sqrt2, U = theta_out / s
   for (int w = tm.tid; w < 2 * D * Dn; w += tm.nt) {
     const int kap = w / (D * Dn), q = (w / Dn) % D, j = w % Dn;

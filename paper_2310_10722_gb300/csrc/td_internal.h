@@ -44,6 +44,10 @@ struct GateDesc {
   int32_t bond;
   int32_t D, Dn;        // active bond dimension before / after
   double p;             // mechanism probability
+  // 0: the gate (1-p) I x I + p X x X of the detector picture; 1: the diagonal gate
+  // diag(w(r + s_a + s_b)), w = (1-p, p), of the generator picture (Sec. 3.2) with the bit r
+  // read from column rcol of the shot's detector row
+  int32_t diag, rcol;
 };
 
 // Site-local operator applied at the start of a layer: psi <- X^{m} K psi on the
@@ -140,10 +144,24 @@ struct Plan {
   std::vector<int64_t> ckpt_lam_off;     // [nseg] checkpointed bond weights (segments >= 1)
   int64_t ckpt_shot_elems = 0;
   int64_t max_site_elems = 0;            // largest site tensor of the sweep (elements)
+  // Generator network (Sec. 3.2, built by build_gen_plan): a row of the sweep's detector
+  // buffer is a representative error r in column order (the edge entering each (site, layer)
+  // from below at t * S + site, then the in-layer edges); n_det = n_qubits is the row length.
+  // The representative of a syndrome m is linear in m: bit i < gen_rank of the elimination
+  // transform gives r at column gen_col[i] (r is zero elsewhere), the bits rank <= i <
+  // n_checks vanish exactly when m is a syndrome, the last row gives the class of r.
+  int32_t gen = 0;
+  int32_t n_checks = 0, n_qubits = 0, n_gen = 0, gen_rank = 0, check_words = 0;
+  std::vector<uint64_t> gen_rows;        // [n_checks + 1][check_words]
+  std::vector<int32_t> gen_col;          // [gen_rank]
+  std::vector<uint8_t> gen_xbar;         // [n_qubits] xbar in column order
+  double gen_log_offset = 0.0;           // -(n_gen - rank of the generators) ln 2
 };
 
 // Build the plan from the ABI structures.  Returns TD_OK or an error with `err` set.
 td_status build_plan(const td_dem& dem, const td_layout& layout, const td_options& opt, Plan& plan,
                      std::string& err);
+// Build the generator network of a CSS sector (td_gen, Sec. 3.2).
+td_status build_gen_plan(const td_gen& gen, const td_options& opt, Plan& plan, std::string& err);
 
 }  // namespace td

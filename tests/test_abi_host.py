@@ -114,3 +114,77 @@ def test_unknown_precision_and_check_without_network(lib):
     dem = point_sector_3d(3, 0.05)
     assert _build(lib, dem, precision=3)[0] == 1
     assert lib.td_network_check(None, None) == 1
+
+
+def _build_gen(lib, gp, **kw):
+    """td_build_gen_network on a td_inputs.GenProblem; keyword overrides of the arrays."""
+    from paper_2310_10722_gb300 import _lib
+    qg = np.ascontiguousarray(kw.pop("qubit_gens", [list(e) + [-1] * (2 - len(e)) for e in gp.edges]),
+                              dtype=np.int32).reshape(-1)
+    p = np.ascontiguousarray(kw.pop("p", gp.p), dtype=np.float64)
+    xyt = np.ascontiguousarray(kw.pop("gen_xyt", gp.gen_xyt), dtype=np.int32).reshape(-1)
+    hip, hix = gp.face_dem.H_csr()
+    hip = np.ascontiguousarray(hip, dtype=np.int32)
+    hix = np.ascontiguousarray(hix, dtype=np.int32)
+    xb = np.ascontiguousarray(kw.pop("xbar", gp.xbar), dtype=np.int32)
+    zb = np.ascontiguousarray(kw.pop("zbar", gp.zbar), dtype=np.int32)
+    P = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+    g = _lib.td_gen(len(xyt) // 3, len(qg) // 2, len(hip) - 1, P(qg, C.c_int32), P(p, C.c_double),
+                    P(xyt, C.c_int32), P(hip, C.c_int32), P(hix, C.c_int32), len(xb), P(xb, C.c_int32),
+                    len(zb), P(zb, C.c_int32))
+    o = _lib.td_options()
+    lib.td_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    st = lib.td_build_gen_network(C.byref(g), C.byref(o), C.byref(h))
+    if st == 0:
+        lib.td_free_network(h)
+    return st, lib.td_last_error().decode()
+
+
+def test_generator_network_validation(lib):
+    from td_inputs import loop_sector_3d
+    gp = loop_sector_3d(3, 0.1)
+    # a valid problem gets past validation (then needs a device: OOM / CUDA without a GPU)
+    st, _ = _build_gen(lib, gp)
+    assert st in (0, 3, 4)
+    st, msg = _build_gen(lib, gp, p=np.full(gp.n_qubits, 1.5))
+    assert st == 1 and "rate" in msg
+    # xbar with a syndrome: drop one of its qubits
+    st, msg = _build_gen(lib, gp, xbar=list(gp.xbar)[1:])
+    assert st == 1 and "xbar" in msg
+    # zbar that anticommutes with a generator: drop its top qubit
+    st, msg = _build_gen(lib, gp, zbar=list(gp.zbar)[:-1])
+    assert st == 1 and "zbar" in msg
+    # xbar and zbar commuting: take zbar = xbar's complement overlap even (empty zbar)
+    st, msg = _build_gen(lib, gp, zbar=[])
+    assert st == 1 and "odd" in msg
+    # a generator that anticommutes with a check: reroute one edge to a far generator
+    qg = [list(e) + [-1] * (2 - len(e)) for e in gp.edges]
+    j = next(k for k, e in enumerate(gp.edges) if len(e) == 2)
+    qg[j] = [qg[j][0], gp.n_gen - 1 if qg[j][0] != gp.n_gen - 1 else 0]
+    st, msg = _build_gen(lib, gp, qubit_gens=qg)
+    assert st in (1, 2) and msg
+    # bad generator index
+    qg = [list(e) + [-1] * (2 - len(e)) for e in gp.edges]
+    qg[0] = [gp.n_gen, -1]
+    st, msg = _build_gen(lib, gp, qubit_gens=qg)
+    assert st == 1 and "range" in msg
+    st, msg = _build_gen(lib, gp, chi=33)
+    assert st == 7
+
+
+def test_generator_network_geometry_rules(lib):
+    from td_inputs import loop_sector_3d
+    gp = loop_sector_3d(3, 0.1)
+    # move one generator to a layer of its own: a site without a generator in some layer
+    xyt = np.array(gp.gen_xyt).copy()
+    xyt[0, 2] = 5
+    st, msg = _build_gen(lib, gp, gen_xyt=xyt)
+    assert st in (1, 7) and msg
+
+
+def test_generator_calls_on_detector_network_rejected_without_network(lib):
+    assert lib.td_gen_coset_logprob(None, None, 0, None, None) == 1
+    assert lib.td_gen_decode(None, None, 0, None, None, None) == 1
