@@ -240,9 +240,14 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- our arm
 PRECISIONS = {"fp64": 0, "fp32": 1, "tc": 2}
-DTYPES = {"fp64": "f64",
-          "fp32": "f32 storage + bf16 tensor-core Gram slices (exact, FP32 accumulate) + f32/f64 SVDs",
-          "tc": "f64 storage + bf16 tensor-core Gram slices (exact, FP32 accumulate) + f32-preconditioned f64 SVDs"}
+# the arithmetic type of each path, and what computes in it
+DTYPES = {"fp64": "f64", "fp32": "f64", "tc": "f64"}
+PRECISION_DETAIL = {
+    "fp64": "f64 storage and arithmetic on the CUDA cores",
+    "fp32": "f32 storage; Gram from exact bf16 slices on tcgen05 (fp32 TMEM sums, exact), f64 combination; "
+            "f64 update; f32-preconditioned f64 SVDs; f64 final contraction",
+    "tc": "f64 storage; Gram from exact bf16 slices on tcgen05 (fp32 TMEM sums, exact), f64 combination; "
+          "f64 update; f32-preconditioned f64 SVDs; f64 final contraction"}
 
 
 def _f(x, digits=4):
@@ -412,7 +417,9 @@ def main():
         ach, peak, unit, bound = wf * shots_done / (ms / 1000.0) / 1e12, fma64, "TFLOP/s", "alu"
         src = "FP64 FMA throughput measured in this run by td_measure_fma_peak (of measured)"
     roof = {"kernel": f"k_{dom}", "bound": bound, "achieved": _f(ach), "peak": _f(peak), "unit": unit,
-            "frac": _f(ach / peak, 3), "traffic": KERNEL_TRAFFIC.get((dom, args.precision, chi)),
+            "frac": _f(ach / peak, 3), "traffic": (_f(KERNEL_TRAFFIC[(dom, args.precision, chi)][0] * shots_done / max(launches, 1))
+                        if (dom, args.precision, chi) in KERNEL_TRAFFIC else None),
+            "traffic_source": (KERNEL_TRAFFIC.get((dom, args.precision, chi)) or (None, None))[1],
             "peak_source": src, "avg_launch_ms": _f(ms / max(launches, 1)), "time_share": _f(ms / tot_ms, 3),
             "flops_per_shot": _f(wf), "fp64_flops_per_shot": _f(wf64)}
 
@@ -543,7 +550,8 @@ def main():
         "metric": METRIC, "value": _f(value), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": _f(1000.0 * t_max / args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision], "data": "synthetic",
-        "config": {"workload": workload(chi), "precision": args.precision, "shots_per_gpu": SHOTS,
+        "config": {"workload": workload(chi), "precision": args.precision,
+                   "precision_detail": PRECISION_DETAIL[args.precision], "shots_per_gpu": SHOTS,
                    "wave": info["wave"], "parallelism": f"replicas x{world}", "schedule": schedule,
                    "l2": "not flushed: every step rewrites %.1f GB of site tensors, far above the 129 MB L2"
                          % (info["workspace_bytes"] / 1e9)},
@@ -566,7 +574,17 @@ def main():
 # DRAM traffic per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (kernel class, precision, chi); see profiles/.  None until a
 # capture of the current kernel exists.
-KERNEL_TRAFFIC = {}
+# DRAM bytes per launch of the dominant kernel (ncu dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (kernel class, precision, chi): (bytes, how they were obtained).  None once the
+# kernel has changed since the capture.
+# DRAM bytes per shot of the dominant kernel (ncu dram__bytes_read.sum + dram__bytes_write.sum of
+# one launch, divided by its shots), keyed by (kernel class, precision, chi): (bytes per shot,
+# how they were obtained).  The line reports them x the shots of one launch (one block per shot,
+# so the traffic grows with the shots).  Remove an entry when its kernel changes.
+KERNEL_TRAFFIC = {
+    ("final", "tc", 8): (9.765e9 / 1024, "one k_final launch over 1024 shots: 3.170 GB read + 6.595 GB written "
+                                         "(profiles/k_final_dram_rotated_d9_chi8_tc.md), scaled to this launch's shots"),
+}
 
 
 if __name__ == "__main__":
