@@ -197,7 +197,18 @@ static void final_layout(td_network* net, int threads, bool allow_smem = true) {
       mR = std::max<int64_t>(mR, (int64_t)m * td::bank_ld32(m, g));
     }
   }
-  const int64_t mQ = (int64_t)cmx * Dm * 2 * cm * Dm;
+  int64_t mQ = (int64_t)cmx * Dm * 2 * cm * Dm;
+  {
+    // wide cuts (n < m): M (m x n) with the leading dimension of an n-column Jacobi (in the
+    // QR copy's region) and its n x n rotation (in V's region)
+    const int m_max = cm * Dm;
+    for (int m = 2; m <= m_max; ++m)
+      for (int n = 1; n < m; ++n) {
+        const int g = td::team_svd_group(threads, m, n);
+        mQ = std::max<int64_t>(mQ, (int64_t)n * td::bank_ld32(m, g));
+        mV = std::max<int64_t>(mV, (int64_t)n * td::bank_ld32(n, g));
+      }
+  }
   const int64_t mP = (int64_t)(cm * Dm + 1) * cm * Dm, mT = (int64_t)cm * Dm * cm * Dm;
   const int64_t mW = std::max<int64_t>({(int64_t)cm * Dm * 2 * Dm * cmx, mV, mR});
   const int64_t mC = (int64_t)cm * cmx * Dm * 2;

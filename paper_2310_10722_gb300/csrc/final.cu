@@ -30,13 +30,14 @@
 
 namespace td {
 
-// F[c][l][r][d][u] of site (x, y) into F (dims into fd: L, R, D, U).  sqrt(lambda) of the
-// site's bonds is staged in slam[4][chi] first.
+// F[c][l][r][d][u] of site (x, y) into F (dims into fd: L, R, D, U; fd[4] = 1 when the
+// class-1 half F[1] can be nonzero, 0 when it is exactly zero -- the readout has no class
+// flip).  sqrt(lambda) of the site's bonds is staged in slam[4][chi] first.
 template <typename T, typename R>
 __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y, R* F, int* fd, R* slam) {
   const int s = fa.grid_site[y * fa.nx + x];
   if (s < 0) {
-    if (tm.tid == 0) { F[0] = R(1); F[1] = R(0); }
+    if (tm.tid == 0) { F[0] = R(1); F[1] = R(0); fd[4] = 0; }
     if (tm.tid < 4) fd[tm.tid] = 1;
     tm.sync();
     return;
@@ -83,7 +84,12 @@ __device__ void build_F(const Team& tm, const FinalArgs& fa, int b, int x, int y
     F[w] = a0 * wgt;
     F[rest + w] = a1 * wgt;
   }
-  if (tm.tid == 0) { fd[0] = dL; fd[1] = dR; fd[2] = dD; fd[3] = dU; }
+  if (tm.tid == 0) {
+    fd[0] = dL; fd[1] = dR; fd[2] = dD; fd[3] = dU;
+    int c1 = 0;
+    for (int ph = 0; ph < fs.P; ++ph) c1 |= (Rv[ph * 2 + 1] != 0.0);
+    fd[4] = c1;
+  }
   tm.sync();
 }
 
@@ -105,7 +111,7 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
   R* sv = work + fa.w_s;
   int* ord = reinterpret_cast<int*>(work + fa.w_ord);
   __shared__ int mdim[2][kMaxGridX][3];   // per column: (left, down, right) of the MPS tensors
-  __shared__ int fd[4];
+  __shared__ int fd[5];
   __shared__ int meta[8];
   __shared__ R slam[4 * kMaxChi];
   __shared__ double logsum_s;
@@ -168,6 +174,7 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
       // the Jacobi lane groups of consecutive columns fall on disjoint banks
       const int nF = L * Rr * aD * U;
       const int m = cJ * U, n = aR * Rr * 2;
+      const int pc = fd[4];   // 0: F[1] is zero, so only p = q contributes (half the products)
       const int ldm = bank_ld32(n, team_svd_group(tm.nt, n, m));
       const int ldv = bank_ld32(m, team_svd_group(tm.nt, n, m));
       for (int w = tm.tid; w < m * n; w += tm.nt) {
@@ -175,8 +182,9 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
         const int q = c % 2, r = (c / 2) % Rr, bb = c / (2 * Rr);
         const int j = ju / U, u = ju % U;
         R acc = R(0);
+        const int p_lo = pc ? 0 : q, p_hi = pc ? 2 : q + 1;
         for (int l = 0; l < L; ++l)
-          for (int p = 0; p < 2; ++p) {
+          for (int p = p_lo; p < p_hi; ++p) {
             const R* t1 = T1 + (((l * 2 + p) * aD) * aR + bb) * cJ + j;
             const R* f = F + (p ^ q) * nF + ((l * Rr + r) * aD) * U + u;
             for (int d = 0; d < aD; ++d) acc += t1[d * aR * cJ] * f[d * U];
@@ -191,8 +199,24 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
         // the columns of the triangular factor of MT's QR (see the file comment)
         R* V = W;
         const bool qr = !rs && m >= 2 && n >= m;
+        // a wide cut (n < m: the first row, where the incoming MPS has bond 1) has rank <= n:
+        // one-sided Jacobi on the n columns of M (not the m columns of M^T); the left singular
+        // vectors are M's rotated columns, normalised
+        const bool wide = !rs && n < m;
+        const int nc = wide ? n : m;   // singular values computed
+        R* Mt = work + fa.w_Q;
+        const int ldt = bank_ld32(m, team_svd_group(tm.nt, m, n));
         int ldvv = ldv;
-        if (qr) {
+        if (wide) {
+          for (int w = tm.tid; w < m * n; w += tm.nt) {
+            const int c = w / m, ju = w % m;
+            Mt[c * ldt + ju] = MT[ju * ldm + c];
+          }
+          tm.sync();
+          ldvv = bank_ld32(n, team_svd_group(tm.nt, m, n));
+          team_svd_onesided<R>(tm, Mt, ldt, m, n, V, ldvv, meta + 7, 40, true);
+          team_col_norms<R>(tm, Mt, ldt, m, n, sv);
+        } else if (qr) {
           R* Qw = work + fa.w_Q;
           R* Rk = work + fa.w_R;
           const int ldr = bank_ld32(m, team_svd_group(tm.nt, m, m));
@@ -208,7 +232,7 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
           if constexpr (sizeof(R) == 8) {
             if (fa.precond)
               svd_precond(tm, Rk, ldr, m, m, V, ldvv, work + fa.w_P, work + fa.w_T, meta + 7, &slot_s,
-                          fa.chi_mps + 2 < m ? fa.chi_mps + 2 : 0, sv, ord);
+                          fa.chi_mps + 2 < m ? fa.chi_mps + 2 : 0, sv, ord, true);
             else
               team_svd_onesided<R>(tm, Rk, ldr, m, m, V, ldvv, meta + 7, 40, true);
           } else {
@@ -219,7 +243,7 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
           team_svd_onesided<R>(tm, MT, ldm, n, m, V, ldv, meta + 7, 40, true);
           team_col_norms<R>(tm, MT, ldm, n, m, sv);
         }
-        team_sort_desc<R>(tm, sv, m, ord);
+        team_sort_desc<R>(tm, sv, nc, ord);
         if (tm.tid == 0) {
           int k = 0;
           const R s0 = sv[ord[0]];
@@ -257,23 +281,38 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
           int e2 = 0;
           frexp(double(sv[ord[0]]), &e2);
           const R inv0 = R(ldexp(1.0, -e2));
-          for (int w = tm.tid; w < m * k; w += tm.nt) {
-            const int ju = w / k, kk = w % k;
-            An[w] = V[ord[kk] * ldvv + ju];
-          }
-          if (qr) {
-            // carry = (M^T V_k)^T from the unreduced M^T
+          if (wide) {
+            for (int w = tm.tid; w < m * k; w += tm.nt) {
+              const int ju = w / k, kk = w % k;
+              An[w] = Mt[ord[kk] * ldt + ju] / sv[ord[kk]];
+            }
+            tm.sync();
+            // carry = (M^T U_k)^T from the unrotated M^T
             for (int w = tm.tid; w < k * n; w += tm.nt) {
               const int kk = w / n, c = w % n;
-              const R* vk = V + ord[kk] * ldvv;
               R acc = R(0);
-              for (int j = 0; j < m; ++j) acc += MT[j * ldm + c] * vk[j];
+              for (int j = 0; j < m; ++j) acc += MT[j * ldm + c] * An[j * k + kk];
               Cn[w] = acc * inv0;
             }
           } else {
-            for (int w = tm.tid; w < k * n; w += tm.nt) {
-              const int kk = w / n, c = w % n;
-              Cn[w] = MT[ord[kk] * ldm + c] * inv0;
+            for (int w = tm.tid; w < m * k; w += tm.nt) {
+              const int ju = w / k, kk = w % k;
+              An[w] = V[ord[kk] * ldvv + ju];
+            }
+            if (qr) {
+              // carry = (M^T V_k)^T from the unreduced M^T
+              for (int w = tm.tid; w < k * n; w += tm.nt) {
+                const int kk = w / n, c = w % n;
+                const R* vk = V + ord[kk] * ldvv;
+                R acc = R(0);
+                for (int j = 0; j < m; ++j) acc += MT[j * ldm + c] * vk[j];
+                Cn[w] = acc * inv0;
+              }
+            } else {
+              for (int w = tm.tid; w < k * n; w += tm.nt) {
+                const int kk = w / n, c = w % n;
+                Cn[w] = MT[ord[kk] * ldm + c] * inv0;
+              }
             }
           }
           if (tm.tid == 0) {

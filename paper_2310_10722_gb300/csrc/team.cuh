@@ -526,7 +526,7 @@ __device__ __forceinline__ void team_gemm(const Team& tm, const R* A, int lda, c
 // accuracy, give the remaining singular values to FP32 relative accuracy.
 __device__ inline void svd_precond(const Team& tm, double* A, int lda, int m, int n, double* V, int ldv, double* F,
                                    double* Tt, int* flag, double* slot, int ktop = 0, double* nrm = nullptr,
-                                   int* ord = nullptr) {
+                                   int* ord = nullptr, bool upper = false) {
   const double amax = team_absmax(tm, A, lda, m, n, slot);
   if (!(amax > 0.0) || n < 2) {
     team_svd_onesided<double>(tm, A, lda, m, n, V, ldv, flag, 40, true);
@@ -547,14 +547,21 @@ __device__ inline void svd_precond(const Team& tm, double* A, int lda, int m, in
     V[c * ldv + r] = double(V32[c * lv32 + r]);
   }
   tm.sync();
-  // Newton-Schulz: V <- V (3I - V^T V) / 2   (Tt, F: column-major, ld n)
-  for (int w = tm.tid; w < n * n; w += tm.nt) {
-    const int j = w / n, i = w % n;
+  // Newton-Schulz: V <- V (3I - V^T V) / 2   (Tt, F: column-major, ld n); V^T V is
+  // symmetric: the entries i <= j are computed and mirrored (the same products in the same
+  // order, so the mirror is exact)
+  for (int w = tm.tid; w < n * (n + 1) / 2; w += tm.nt) {
+    int j = (int)((sqrt(8.0 * w + 1.0) - 1.0) * 0.5);
+    while ((j + 1) * (j + 2) / 2 <= w) ++j;
+    while (j * (j + 1) / 2 > w) --j;
+    const int i = w - j * (j + 1) / 2;   // 0 <= i <= j
     const double* vi = V + i * ldv;
     const double* vj = V + j * ldv;
     double s = 0.0;
     for (int l = 0; l < n; ++l) s += vi[l] * vj[l];
-    Tt[j * n + i] = (i == j ? 1.5 : 0.0) - 0.5 * s;
+    const double t = (i == j ? 1.5 : 0.0) - 0.5 * s;
+    Tt[j * n + i] = t;
+    Tt[i * n + j] = t;
   }
   tm.sync();
   for (int w = tm.tid; w < n * n; w += tm.nt) {
@@ -566,11 +573,12 @@ __device__ inline void svd_precond(const Team& tm, double* A, int lda, int m, in
   tm.sync();
   for (int w = tm.tid; w < n * n; w += tm.nt) V[(w / n) * ldv + (w % n)] = F[w];
   tm.sync();
-  // A <- A V   (F: column-major, ld m)
+  // A <- A V   (F: column-major, ld m); an upper-triangular A (row i zero in columns < i)
+  // skips the zero products
   for (int w = tm.tid; w < m * n; w += tm.nt) {
     const int j = w / m, i = w % m;
     double s = 0.0;
-    for (int l = 0; l < n; ++l) s += A[l * lda + i] * V[j * ldv + l];
+    for (int l = upper ? i : 0; l < n; ++l) s += A[l * lda + i] * V[j * ldv + l];
     F[j * m + i] = s;
   }
   tm.sync();
