@@ -339,7 +339,8 @@ td_status td_network_profile(td_network* net, int32_t enable, double* ms, int64_
  * bytes = minimum device-memory traffic (each tensor a kernel must read or write, once);
  * flops = multiply-adds x 2 of the contractions, plus textbook counts for the dense
  * factorisations (symmetric eigensolver with vectors 9n^3; SVD of m x n, m >= n, with both
- * factors 4m^2 n + 8m n^2 + 9n^3).  fp64_flops = the part of flops done in FP64. */
+ * factors 4m^2 n + 8m n^2 + 9n^3 in the truncation cores; the zip-up cuts need the singular
+ * values and the left factor only: 6m n^2 + 11n^3, or 2n m^2 + 11m^3 for m < n).  fp64_flops = the part of flops done in FP64. */
 td_status td_network_get_work(const td_network* net, double* bytes, double* flops, double* fp64_flops);
 
 /* Measurement helper for roofline denominators (no counterpart in the paper): the fused

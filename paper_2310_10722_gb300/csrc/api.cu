@@ -1271,6 +1271,12 @@ td_status td_network_get_work(const td_network* net, double* bytes, double* flop
     if (m < n) std::swap(m, n);
     return 4.0 * m * m * n + 8.0 * m * n * n + 9.0 * n * n * n;
   };
+  // singular values and left singular vectors of an m x n matrix (a zip-up cut keeps left
+  // vectors only): R-SVD counts, Sigma and U1 (6 m n^2 + 11 n^3) for m >= n, Sigma and the
+  // square left factor through a QR of the transpose (2 n m^2 + 11 m^3) for m < n
+  auto svd_left = [](double m, double n) {
+    return m >= n ? 6.0 * m * n * n + 11.0 * n * n * n : 2.0 * n * m * m + 11.0 * m * m * m;
+  };
   bytes[TD_K_INIT] = 0;
   for (const td::LocalDesc& d : P.locals) {
     bytes[TD_K_LOCAL] += 2.0 * d.P * d.rest * el;
@@ -1312,10 +1318,14 @@ td_status td_network_get_work(const td_network* net, double* bytes, double* flop
         bytes[TD_K_FINAL] += f.P * rest * el;
       }
       const double aL = mL[x], aD = mDn[x], aR = mR[x];
-      flops[TD_K_FINAL] += 2.0 * cJ * L * 2 * aD * aR * aL + 2.0 * cJ * U * aR * R * 2 * (L * 2 * aD);
+      // the site's class-1 half is zero when its readout flips no class: one parity term
+      double cls1 = 0;
+      if (s >= 0)
+        for (int ph = 0; ph < P.finals[s].P; ++ph) cls1 = cls1 || P.finals[s].R[ph * 2 + 1] != 0.0;
+      flops[TD_K_FINAL] += 2.0 * cJ * L * 2 * aD * aR * aL + 2.0 * cJ * U * aR * R * 2 * (L * (cls1 ? 2 : 1) * aD);
       const double m = cJ * U, n = aR * R * 2;
       if (x < P.nx - 1 && y < P.ny - 1) {
-        flops[TD_K_FINAL] += svd(m, n);
+        flops[TD_K_FINAL] += svd_left(m, n);
         const double k = std::min<double>(P.chi_mps, std::min(m, n));
         nL[x] = cJ; nD[x] = U; nR[x] = k;
         cJ = k;
