@@ -303,6 +303,7 @@ def main():
     ap.add_argument("--chi16-shots", type=int, default=256, help="shots of the chi = 16 line")
     ap.add_argument("--uneven-per-size", type=int, default=152, help="shots per code size of the uneven batch")
     ap.add_argument("--loop-shots", type=int, default=1024, help="shots of the loop-sector line")
+    ap.add_argument("--chi32-shots", type=int, default=0, help="shots of the chi = 32 line (0: skipped)")
     args = ap.parse_args()
     SHOTS = args.shots
     rank = int(os.environ.get("RANK", "0"))
@@ -451,6 +452,24 @@ def main():
         extra["rotated_d9_chi16_mps16"] = {"shots": n16, "fp64": r16["fp64"], args.precision: r16[args.precision],
                                            "max_dlogp_coset": st16["max_dlogp_coset"],
                                            "max_dlogp_decision_coset": st16["max_dlogp_decision_coset"]}
+
+    # rotated d = 9 at chi = 32, chi_mps = 8 on --chi32-shots shots (off by default: ~1 GB of
+    # site tensors per shot and seconds per shot even on the GPU)
+    if not args.no_extra and rank == 0 and args.chi32_shots > 0:
+        n32 = args.chi32_shots
+        d32 = det[:n32].contiguous()
+        r32, lps32 = {}, {}
+        for name, pv in (("fp64", 0), (args.precision, prec)):
+            nx = td.Network.from_dem(dem, chi=32, chi_mps=8, precision=pv, mem_budget=200 << 30)
+            nx.coset_logprob(d32[:2])
+            torch.cuda.synchronize()
+            lps32[name], mx = timed_decode(nx, d32, stream)
+            nx.check()
+            r32[name] = _f(n32 / (mx / 1000.0))
+            nx.close()
+        st32 = coset_stats(lps32[args.precision], lps32["fp64"])
+        extra["rotated_d9_chi32_mps8"] = {"shots": n32, "fp64": r32["fp64"], args.precision: r32[args.precision],
+                                          "max_dlogp_coset": st32["max_dlogp_coset"]}
 
     # uneven batch: point-sector codes d = 5, 7, 9, 11 decoded together, their decode calls
     # captured once in a CUDA graph and replayed (one network per code size)

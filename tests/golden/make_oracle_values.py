@@ -4,8 +4,8 @@ Each case is a seeded workload decoded by the same-chi FP64 sweep of the oracle
 (oracle/su.py, Sec. 4 of the paper).  The GPU tests regenerate the same detector bits from
 the seeded stream (td_inputs) and compare element by element.  Run from the repository
 root:  python tests/golden/make_oracle_values.py [--jobs N]
-The oracle takes about 1 s (rotated d = 9, chi = 8) to 5 s (chi = 16) per shot; the cases
-are split over N spawned processes.
+The oracle takes about 1 s (rotated d = 9, chi = 8), 5 s (chi = 16) and several minutes
+(chi = 32) per shot; the cases are split over N spawned processes (--only NAME: one case).
 """
 from __future__ import annotations
 
@@ -25,6 +25,7 @@ CASES = {
     "rotated_d9_r9_p0.03_chi8_mps8": ("rotated", (9, 9, 0.03, 0.03), 2000, 64, 8, 8),
     "rotated_d9_r9_p0.03_chi16_mps16": ("rotated", (9, 9, 0.03, 0.03), 2000, 64, 16, 16),
     "point_d7_p0.1_chi16_mps8": ("point", (7, 0.1), 4007, 48, 16, 8),
+    "rotated_d9_r9_p0.03_chi32_mps8": ("rotated", (9, 9, 0.03, 0.03), 2000, 4, 32, 8),
 }
 
 
