@@ -140,6 +140,18 @@ td_status td_build_network(const td_dem* dem, const td_layout* layout, const td_
 td_status td_coset_logprob(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
                            void* stream);
 
+/* td_coset_logprob with truncation statistics per shot (a property of this library; the
+ * paper reports none): stats_dev, device double [B][4], receives for shot b
+ *   [b][0], [b][1]: the largest and the sum over the simple-update truncations (Sec. 4) of
+ *                   the discarded fraction sum_{i >= k} s_i^2 / sum_i s_i^2 of the bond's
+ *                   singular values s (the squared Frobenius error of that truncation relative
+ *                   to the squared norm of the two-site tensor under the bond's environment);
+ *   [b][2], [b][3]: the same over the cuts of the final boundary-MPS contraction.
+ * Zero where nothing was truncated (values below svd_cutoff * s_1 dropped count, ~1e-24).
+ * Overwrites stats_dev[0 .. B); logp_dev as td_coset_logprob.  Asynchronous on `stream`. */
+td_status td_coset_logprob_stats(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
+                                 double* stats_dev, void* stream);
+
 /* Decisions L*(m) = argmax_L p_{m,L} (Sec. 2.4; ties -> lowest L) and margins
  * log p_{m,L*} - max_{L != L*} log p_{m,L}.  decision_dev: device int32 [B];
  * margin_dev: device double [B] or NULL.  Asynchronous on `stream`. */

@@ -223,6 +223,14 @@ class ZeroProbability(Exception):
     pass
 
 
+def discarded_fraction(sv: np.ndarray, k: int) -> float:
+    """Weight a truncation to k singular values drops: sum_{i >= k} s_i^2 / sum_i s_i^2 (the
+    squared Frobenius error of the truncated matrix relative to its squared norm)."""
+    s2 = np.asarray(sv, dtype=np.float64) ** 2
+    tot = s2.sum()
+    return float(s2[k:].sum() / tot) if tot > 0 else 0.0
+
+
 def _scale_axis(A, ax, w):
     shape = [1] * A.ndim
     shape[ax] = -1
@@ -239,6 +247,7 @@ class PEPS:
             self.G.append(g)
         self.lam = [np.ones(1) for _ in plan.bonds]
         self.logscale = 0.0
+        self.trunc = []          # discarded fraction of every simple-update truncation
 
     def apply_local(self, s, M):
         self.G[s] = np.tensordot(M, self.G[s], axes=(1, 0))
@@ -284,6 +293,7 @@ class PEPS:
         if sv[0] <= 0:
             raise ZeroProbability
         k = keep_count(sv, chi, cutoff, mrtol)
+        self.trunc.append(discarded_fraction(sv, k))
         newM = (QA @ U[:, :k], QB @ Vt[:k].T)
         self.lam[bond] = sv[:k] / sv[0]
         self.logscale += np.log(sv[0])
@@ -317,7 +327,7 @@ class PEPS:
         return out
 
 
-def boundary_mps(plan: SUPlan, F, chi_mps: int, cutoff: float, mrtol: float):
+def boundary_mps(plan: SUPlan, F, chi_mps: int, cutoff: float, mrtol: float, trunc: list | None = None):
     """Zip-up boundary-MPS contraction of the final 2D network with a class-parity leg.
 
     Returns (Z[2], logscale): Z[c] * exp(logscale) = sum over readouts with total class c.
@@ -351,6 +361,8 @@ def boundary_mps(plan: SUPlan, F, chi_mps: int, cutoff: float, mrtol: float):
                     if sv[0] <= 0:
                         raise ZeroProbability
                     k = keep_count(sv, chi_mps, cutoff, mrtol)
+                    if trunc is not None:
+                        trunc.append(discarded_fraction(sv, k))
                     new.append(Um[:, :k].reshape(J, U, k))
                     C = ((sv[:k] / sv[0])[:, None] * Vt[:k]).reshape(k, Bd, R, Q)
                     logscale += np.log(sv[0])
@@ -388,7 +400,7 @@ def su_logprob(dem, det_bits: np.ndarray, chi: int, chi_mps: int, cutoff: float 
     return out
 
 
-def _one_shot(plan, m, chi, chi_mps, cutoff, mrtol):
+def _one_shot(plan, m, chi, chi_mps, cutoff, mrtol, stats=None):
     peps = PEPS(plan)
     for t in range(plan.T):
         for s in range(plan.S):
@@ -404,7 +416,12 @@ def _one_shot(plan, m, chi, chi_mps, cutoff, mrtol):
         for bond, p, ma, mb in plan.gates[t]:
             peps.gate(bond, p, ma, mb, chi, cutoff, mrtol)
     F = peps.final_tensors()
-    Z, ls = boundary_mps(plan, F, chi_mps, cutoff, mrtol)
+    cuts = []
+    Z, ls = boundary_mps(plan, F, chi_mps, cutoff, mrtol, cuts)
+    if stats is not None:
+        su_t = peps.trunc or [0.0]
+        mps_t = cuts or [0.0]
+        stats[:] = [max(su_t), sum(su_t), max(mps_t), sum(mps_t)]
     for l, p in plan.glob:
         if l:
             Z = np.array([(1 - p) * Z[0] + p * Z[1], (1 - p) * Z[1] + p * Z[0]])
@@ -414,6 +431,23 @@ def _one_shot(plan, m, chi, chi_mps, cutoff, mrtol):
     with np.errstate(divide="ignore"):
         logZ = np.log(np.where(Z > 0, Z, 0.0)) + ls + peps.logscale
     return np.array([logZ[0 ^ off], logZ[1 ^ off]])
+
+
+def su_truncation_stats(dem, det_bits: np.ndarray, chi: int, chi_mps: int, cutoff: float = 1e-12,
+                        mrtol: float = 1e-8, plan: SUPlan | None = None) -> np.ndarray:
+    """Per shot [B, 4]: the largest and the summed discarded fraction (discarded_fraction) of
+    the simple-update truncations, then of the zip-up cuts, of the sweep of su_logprob.  Shots
+    whose sweep meets a zero probability before its end keep what was recorded (zeros)."""
+    plan = plan or SUPlan(dem)
+    out = np.zeros((det_bits.shape[0], 4))
+    for b in range(det_bits.shape[0]):
+        st = [0.0] * 4
+        try:
+            _one_shot(plan, det_bits[b], chi, chi_mps, cutoff, mrtol, st)
+        except ZeroProbability:
+            pass
+        out[b] = st
+    return out
 
 
 def plan_det(plan, s, t):

@@ -103,6 +103,19 @@ class Network:
                                          self._stream(stream)))
         return out
 
+    def coset_logprob_stats(self, det, stream=None):
+        """(log p_{m,L} [B, 2], truncation statistics [B, 4]) on the device: per shot the
+        largest and the summed discarded fraction of the simple-update truncations, then of
+        the final contraction's cuts (td_coset_logprob_stats)."""
+        import torch
+        self._check_det(det)
+        B = det.shape[0]
+        out = torch.empty((B, self.n_class), dtype=torch.float64, device=det.device)
+        stats = torch.empty((B, 4), dtype=torch.float64, device=det.device)
+        check(self._lib.td_coset_logprob_stats(self._h, C.c_void_p(det.data_ptr()), B, C.c_void_p(out.data_ptr()),
+                                               C.c_void_p(stats.data_ptr()), self._stream(stream)))
+        return out, stats
+
     def decode(self, det, stream=None):
         """(decision int32 [B], margin float64 [B]) on the device."""
         import torch

@@ -409,8 +409,12 @@ struct NetProf : td::Prof {
 
 static td_status run(td_network* net, const uint8_t* det, int64_t B, double* logp, int32_t* decision, double* margin,
                      cudaStream_t st, void* final_scratch = nullptr, const td::VShot* vs = nullptr,
-                     const td::Override* ovr = nullptr) {
+                     const td::Override* ovr = nullptr, double* stats = nullptr) {
   td::Plan& P = net->plan;
+  if (stats && B > 0) {
+    const cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(double) * 4 * (size_t)B, st);
+    if (e != cudaSuccess) return cuda_fail(e, "statistics reset");
+  }
   NetProf prof(net, st);
   for (int64_t w0 = 0; w0 < B; w0 += net->wave) {
     const int32_t Bw = (int32_t)std::min<int64_t>(net->wave, B - w0);
@@ -435,6 +439,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     a.tc = P.precision == TD_FP64 ? 0 : 1;
     a.precond = P.precision == TD_FP64 ? 0 : 1;
     a.status = net->d_status;
+    a.stats = stats;
     const bool f64 = P.precision != TD_FP32;   // storage type
     cudaError_t e;
     {
@@ -480,6 +485,7 @@ static td_status run(td_network* net, const uint8_t* det, int64_t B, double* log
     f.vs = vs;
     f.ovr = ovr;
     f.wave_first = (int32_t)w0;
+    f.stats = stats;
     {
       td_network::Mark mk(net, TD_K_FINAL, st);
       e = f64 ? td::launch_final<double, double>(f, st) : td::launch_final<float, double>(f, st);
@@ -524,6 +530,16 @@ td_status td_coset_logprob(td_network* net, const uint8_t* det_dev, int64_t B, d
   if (s != TD_OK) return s;
   if (B > 0 && !logp_dev) return fail(TD_ERR_INVALID, "null output buffer");
   return run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+td_status td_coset_logprob_stats(td_network* net, const uint8_t* det_dev, int64_t B, double* logp_dev,
+                                 double* stats_dev, void* stream) {
+  g_err.clear();
+  td_status s = check_call(net, det_dev, B);
+  if (s != TD_OK) return s;
+  if (B > 0 && (!logp_dev || !stats_dev)) return fail(TD_ERR_INVALID, "null output buffer");
+  return run(net, det_dev, B, logp_dev, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr,
+             nullptr, stats_dev);
 }
 
 td_status td_decode(td_network* net, const uint8_t* det_dev, int64_t B, int32_t* decision_dev, double* margin_dev,

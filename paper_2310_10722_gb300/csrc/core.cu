@@ -183,6 +183,20 @@ __global__ void k_core2(SweepArgs a, const GateDesc* __restrict__ gates, const d
     int k = 0;
     if (srt[0] > 0.0) k = team_keep_count<double>(srt, rB < rA ? rB : rA, Dn, a.svd_cutoff, a.multiplet_rtol);
     meta[0] = k;
+    if (a.stats && k > 0) {
+      // discarded fraction sum_{j >= k} s_j^2 / sum_j s_j^2; the shot's gates of a round run
+      // concurrently: the max on the bit patterns (non-negative doubles order as them)
+      double tot = 0.0, disc = 0.0;
+      for (int j = 0; j < rB; ++j) {
+        const double q = srt[j] * srt[j];
+        tot += q;
+        if (j >= k) disc += q;
+      }
+      const double f = tot > 0.0 ? disc / tot : 0.0;
+      double* st = a.stats + (int64_t)(a.wave_first + b) * 4;
+      atomicMax(reinterpret_cast<unsigned long long*>(st), (unsigned long long)__double_as_longlong(f));
+      atomicAdd(st + 1, f);
+    }
   }
   tm.sync();
   const int k = meta[0];

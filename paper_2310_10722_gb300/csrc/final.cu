@@ -115,10 +115,11 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
   __shared__ int meta[8];
   __shared__ R slam[4 * kMaxChi];
   __shared__ double logsum_s;
+  __shared__ double trunc_s[2];   // largest and summed discarded fraction of the cuts
   __shared__ R red_s[2];
   __shared__ double slot_s;
   const int nx = fa.nx, ny = fa.ny;
-  if (tm.tid == 0) logsum_s = 0.0;
+  if (tm.tid == 0) { logsum_s = 0.0; trunc_s[0] = 0.0; trunc_s[1] = 0.0; }
   for (int x = tm.tid; x < nx; x += tm.nt) {
     mdim[0][x][0] = 1; mdim[0][x][1] = 1; mdim[0][x][2] = (x == nx - 1) ? 2 : 1;
     R* A = mps[0] + (int64_t)x * fa.mps_stride;
@@ -252,6 +253,17 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
             const int nsv = m < n ? m : n;
             for (int i = 0; i < nsv; ++i) srt[i] = sv[ord[i]];
             k = team_keep_count<R>(srt, nsv, fa.chi_mps, fa.svd_cutoff, fa.multiplet_rtol);
+            if (fa.stats) {   // discarded fraction sum_{i >= k} s_i^2 / sum_i s_i^2
+              double tot = 0.0, disc = 0.0;
+              for (int i = 0; i < nsv; ++i) {
+                const double q = double(srt[i]) * double(srt[i]);
+                tot += q;
+                if (i >= k) disc += q;
+              }
+              const double f = tot > 0.0 ? disc / tot : 0.0;
+              trunc_s[0] = fmax(trunc_s[0], f);
+              trunc_s[1] += f;
+            }
           }
           meta[0] = k;
         }
@@ -398,6 +410,10 @@ __global__ void __launch_bounds__(1024) k_final(FinalArgs fa) {
       fa.Z[(int64_t)b * 2 + 0] = double(v[0]);
       fa.Z[(int64_t)b * 2 + 1] = double(v[1]);
       fa.logacc[(int64_t)b * fa.nslots + fa.slot] = logsum_s;
+      if (fa.stats) {
+        fa.stats[(int64_t)(fa.wave_first + b) * 4 + 2] = trunc_s[0];
+        fa.stats[(int64_t)(fa.wave_first + b) * 4 + 3] = trunc_s[1];
+      }
     }
   }
 }

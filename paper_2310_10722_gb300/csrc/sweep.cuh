@@ -32,6 +32,9 @@ struct SweepArgs {
   int32_t tc;               // Gram pass on the tensor cores (TD_FP32, TD_TC)
   int32_t precond;          // truncation cores: FP32-preconditioned FP64 Jacobi (TD_FP32, TD_TC)
   int* status;              // device status word: a kernel that gives up writes its td_status
+  // truncation statistics (null: none): [call shot][4], entries 0, 1 = the largest and the
+  // summed discarded fraction of the simple-update truncations (index wave_first + b)
+  double* stats;
 };
 
 // Per-gate record of the truncation core for the reverse sweep (doubles), Dm = chi:
@@ -80,6 +83,8 @@ struct FinalArgs {
   // doubles, one slot of rec_slot doubles per (row, column); see FinRecSlot
   double* rec;
   int64_t rec_stride, rec_slot;
+  double* stats;             // truncation statistics (null: none): entries 2, 3 of [call shot][4] = the
+                             // largest and the summed discarded fraction of the zip-up cuts
   int32_t rec_mC, rec_mA, rec_m, rec_n;   // capacities: carry, MPS tensor, cut rows, cut columns
 };
 

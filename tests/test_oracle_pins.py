@@ -252,3 +252,18 @@ def test_planted_zipup_slip_is_caught(monkeypatch):
     ref, _ = zipup_reference(F, 2)
     v, ls = su.boundary_mps(GridPlan(2, 2), F, 2, 1e-12, 1e-8)
     assert np.abs(v * np.exp(ls) - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_discarded_fraction_is_the_relative_truncation_error(seed):
+    """With the environment exact, the weight the truncating gate reports as discarded equals
+    the relative squared error of the optimal truncation of the dense state across that bond
+    (Eckart-Young: the dropped singular values squared over all of them squared); the exact
+    gates discard nothing."""
+    peps, bond, psi = simple_update_case(seed, chi=1)
+    best, s = rank_truncate(psi.reshape(4, 4), 1)
+    want = np.sum((psi.reshape(4, 4) - best) ** 2) / np.sum(psi ** 2)
+    assert want > 1e-8
+    assert peps.trunc[:2] == [0.0, 0.0] or max(peps.trunc[:2]) < 1e-28
+    np.testing.assert_allclose(peps.trunc[2], want, rtol=1e-10)
+    np.testing.assert_allclose(su.discarded_fraction(s, 1), want, rtol=1e-10)
