@@ -293,6 +293,17 @@ td_status td_gen_coset_logprob(td_network* net, const uint8_t* syn_dev, int64_t 
 td_status td_gen_decode(td_network* net, const uint8_t* syn_dev, int64_t B, int32_t* decision_dev,
                         double* margin_dev, void* stream);
 
+/* Diagnostic, no device involved (a property of this library): plan the generator network of
+ * `gen` on the host and evaluate, for each syndrome of syn_host (uint8 [B][n_checks]), the rows
+ * the decoding calls sweep -- rows_host (uint8 [2B][n_qubits]): row 2b = the representative r
+ * of syndrome b in the network's column order, row 2b + 1 = r + xbar -- and cls_host (int32 [B]):
+ * the class r . zbar, or -1 when syndrome b is not a syndrome.  col_host (int32 [n_qubits], or
+ * NULL) receives the column of every qubit: column t * S + s for the edge entering generator
+ * (site s, layer t) from below (layer T: the dangling edge above the last layer; sites in
+ * (y, x) order), then the in-layer edges in qubit order.  Errors as td_build_gen_network. */
+td_status td_gen_rows_host(const td_gen* gen, const uint8_t* syn_host, int64_t B, uint8_t* rows_host,
+                           int32_t* cls_host, int32_t* col_host);
+
 /* Launch schedule of the network (a property of this library; the paper has none): the
  * block size of the final contraction's kernel (256, 512 or 1024 threads; the Jacobi lane
  * groups and the work region's layout follow it), whether that kernel's work region may sit

@@ -18,7 +18,7 @@ EXPORTS = ["td_default_options", "td_build_network", "td_coset_logprob", "td_dec
            "td_network_tune", "td_network_get_info", "td_debug_sweep",
            "td_network_profile", "td_network_get_work", "td_coset_logprob_static", "td_free_network",
            "td_network_check", "td_measure_fma_peak", "td_build_gen_network", "td_gen_coset_logprob",
-           "td_gen_decode", "td_coset_logprob_stats", "td_last_error"]
+           "td_gen_decode", "td_coset_logprob_stats", "td_gen_rows_host", "td_last_error"]
 
 
 class td_dem(C.Structure):
@@ -78,6 +78,8 @@ def load(path: str | None = None):
     lib.td_build_network.restype = C.c_int
     lib.td_coset_logprob.argtypes = [vp, vp, C.c_int64, vp, vp]
     lib.td_coset_logprob.restype = C.c_int
+    lib.td_gen_rows_host.argtypes = [C.POINTER(td_gen), vp, C.c_int64, vp, vp, vp]
+    lib.td_gen_rows_host.restype = C.c_int
     lib.td_coset_logprob_stats.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     lib.td_coset_logprob_stats.restype = C.c_int
     lib.td_decode.argtypes = [vp, vp, C.c_int64, vp, vp, vp]

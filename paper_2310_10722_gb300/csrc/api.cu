@@ -602,6 +602,41 @@ static td_status check_gen_call(td_network* net, const void* syn, int64_t B) {
   return TD_OK;
 }
 
+td_status td_gen_rows_host(const td_gen* gen, const uint8_t* syn_host, int64_t B, uint8_t* rows_host,
+                           int32_t* cls_host, int32_t* col_host) {
+  g_err.clear();
+  if (!gen || B < 0 || (B > 0 && (!syn_host || !rows_host || !cls_host))) return fail(TD_ERR_INVALID, "null argument");
+  td_options o;
+  td_default_options(&o);
+  td::Plan P;
+  std::string err;
+  td_status st = td::build_gen_plan(*gen, o, P, err);
+  if (st != TD_OK) return fail(st, err);
+  const int nq = P.n_qubits, nc = P.n_checks, words = P.check_words;
+  std::vector<uint64_t> mw(words);
+  for (int64_t b = 0; b < B; ++b) {
+    std::fill(mw.begin(), mw.end(), 0ull);
+    for (int c = 0; c < nc; ++c)
+      if (syn_host[b * nc + c] & 1) mw[c / 64] |= 1ull << (c % 64);
+    auto dot = [&](int i) {
+      int par = 0;
+      for (int w = 0; w < words; ++w) par ^= __builtin_popcountll(P.gen_rows[(size_t)i * words + w] & mw[w]);
+      return par & 1;
+    };
+    uint8_t* r0 = rows_host + 2 * b * nq;
+    uint8_t* r1 = r0 + nq;
+    std::fill(r0, r0 + nq, (uint8_t)0);
+    for (int i = 0; i < P.gen_rank; ++i)
+      if (dot(i)) r0[P.gen_col[i]] = 1;
+    int bad = 0;
+    for (int i = P.gen_rank; i < nc; ++i) bad |= dot(i);
+    for (int j = 0; j < nq; ++j) r1[j] = r0[j] ^ P.gen_xbar[j];
+    cls_host[b] = bad ? -1 : dot(nc);
+  }
+  if (col_host) std::copy(P.gen_qcol.begin(), P.gen_qcol.end(), col_host);
+  return TD_OK;
+}
+
 td_status td_gen_coset_logprob(td_network* net, const uint8_t* syn_dev, int64_t B, double* logp_dev, void* stream) {
   g_err.clear();
   td_status s = check_gen_call(net, syn_dev, B);

@@ -756,6 +756,7 @@ td_status build_gen_plan(const td_gen& g, const td_options& opt, Plan& plan, std
     }
     plan.gen_xbar.assign(NQ, 0);
     for (int32_t j = 0; j < NQ; ++j) plan.gen_xbar[col[j]] = xb[j];
+    plan.gen_qcol = col;
   }
   return emit_plan(ns, opt, plan, err);
 }

@@ -155,6 +155,7 @@ struct Plan {
   std::vector<uint64_t> gen_rows;        // [n_checks + 1][check_words]
   std::vector<int32_t> gen_col;          // [gen_rank]
   std::vector<uint8_t> gen_xbar;         // [n_qubits] xbar in column order
+  std::vector<int32_t> gen_qcol;         // [n_qubits] column of every qubit
   double gen_log_offset = 0.0;           // -(n_gen - rank of the generators) ln 2
 };
 
